@@ -1,0 +1,189 @@
+/*
+ * cc_ladder.h -- C ABI of the GB300 (sm_103a) particle-particle ladder library.
+ *
+ * The library evaluates the rate-determining term of the closed-shell CCD/CCSD
+ * vector function with Cholesky-decomposed integrals (arXiv:2310.04559):
+ *
+ *   Eq. 4   0 = ... + sum_cd <ab|cd> t_ij^cd + ...
+ *   Eq. 5   <ab|cd> ~= sum_P L^P_ac L^P_bd
+ *   Eq. 6   R[i,j,a,b] = sum_{c,d} ( sum_P L[P,a,c] L[P,b,d] ) t2[i,j,c,d]
+ *
+ * without ever storing the v^4 integral tensor: the integrals (ac|bd) are
+ * assembled on the device for one block of `a` values at a time (the for-loop
+ * over `a` of Section 3.2, widened to blocks), then contracted with t2.
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ *  - All tensors are row-major, contiguous FP64 (IEEE binary64) DEVICE arrays
+ *    owned by the caller; the library keeps no pointer after a call returns.
+ *      L  [n_chol][v][v]   Cholesky vectors L[P,a,c]        (Eq. 5)
+ *      t2 [o][o][v][v]     amplitudes t2[i,j,c,d]
+ *      R  [o][o][v][v]     result R[i,j,a,b]                (Eq. 6)
+ *    The paper stores amplitudes as t[i,a,j,b] (Section 3.1); a caller with
+ *    that layout permutes axes 1 and 2 first.
+ *  - Every pointer must be 16-byte aligned (CC_ERR_ALIGN otherwise).
+ *  - The library never allocates device memory.  Scratch comes from the
+ *    caller's `workspace` (256-byte aligned); query its size first.  The
+ *    planner sizes the block of `a` values so that the workspace fits the
+ *    caller's budget.
+ *  - Work is enqueued on `stream` (a cudaStream_t; NULL = legacy default
+ *    stream).  Unless CC_FLAG_NO_STATUS_SYNC is given, the call synchronises
+ *    the stream once at the end to read the device status word, so the
+ *    returned status covers device-side failures (CC_ERR_DEVICE_TIMEOUT).
+ *  - Return value: CC_OK (0) or a negative cc_status.  Argument errors are
+ *    detected before anything is enqueued.  No C++ exception crosses the ABI.
+ *  - Thread safety: calls on different streams with different workspaces may
+ *    run concurrently; the plan cache is guarded by a mutex.
+ */
+#ifndef CC_LADDER_H
+#define CC_LADDER_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Status codes. */
+enum cc_status {
+    CC_OK = 0,
+    CC_ERR_SHAPE = -1,          /* o, v or n_chol < 1, or a product overflows      */
+    CC_ERR_NULL = -2,           /* a required pointer is NULL                       */
+    CC_ERR_ALIGN = -3,          /* a pointer is not 16-byte (workspace: 256) aligned */
+    CC_ERR_WORKSPACE = -4,      /* ws_bytes smaller than the plan needs             */
+    CC_ERR_BUDGET = -5,         /* budget below the smallest plan (one `a` per block) */
+    CC_ERR_UNSUPPORTED = -6,    /* mode / order / flag combination not available    */
+    CC_ERR_CUDA = -7,           /* a CUDA runtime call failed                       */
+    CC_ERR_DEVICE_TIMEOUT = -8, /* a bounded device-side wait ran out; results invalid */
+    CC_ERR_ARG = -9             /* other invalid argument (unknown mode, bad a_block) */
+};
+
+/* Arithmetic used for the two contractions (integral build and ladder GEMM). */
+enum cc_precision {
+    CC_FP64 = 0,       /* FP64 tensor-core MMA (DMMA), FP64 accumulation              */
+    CC_OZAKI_BF16 = 1, /* FP64 emulated by split BF16 integer slices (Ozaki scheme) on
+                          tcgen05 tensor cores, exact FP32 slice products, FP64 recombination */
+    CC_OZAKI_INT8 = 2, /* INT8-slice emulation: tcgen05 has no kind::i8 on sm_103a;
+                          always returns CC_ERR_UNSUPPORTED                           */
+    CC_TF32 = 3,       /* TF32 inputs, FP32 accumulation per K-chunk, FP64 across chunks */
+    CC_BF16 = 4        /* BF16 inputs, FP32 accumulation per K-chunk, FP64 across chunks */
+};
+
+/* Contraction order (Section 3.2). */
+enum cc_order {
+    CC_ORDER_AUTO = 0,           /* planner picks the cheaper one for the shape           */
+    CC_ORDER_INTEGRAL_FIRST = 1, /* (ac|bd) block first: 2 n v^4 + 2 o^2 v^4 flops         */
+    CC_ORDER_CHOLESKY_FIRST = 2  /* L.t intermediate first: 4 n o^2 v^3 flops              */
+};
+
+/* Bit flags for cc_ladder_args.flags. */
+enum cc_flags {
+    CC_FLAG_ACCUMULATE = 1,     /* R += term (the paper's `t_new += ...`, Section 3) instead of R = term */
+    CC_FLAG_SYMMETRIC_T = 2,    /* caller promises t2[i,j,c,d] == t2[j,i,d,c]; only pairs i <= j are
+                                   computed and R[j,i,b,a] = R[i,j,a,b] is written by symmetry        */
+    CC_FLAG_EXCHANGE = 4,       /* evaluate the exchange partner of Eq. 7 instead:
+                                   R[i,j,a,b] = sum_cd (sum_P L_Pad L_Pbc) t2[i,j,c,d]                */
+    CC_FLAG_NO_STATUS_SYNC = 8  /* do not synchronise the stream at the end; device-side failures are
+                                   then reported by cc_ladder_device_status()                         */
+};
+
+/* Full argument block for cc_ladder_fwd_ex / cc_ladder_workspace_size_ex. */
+typedef struct cc_ladder_args {
+    int o, v, n_chol;      /* occupied, virtual, Cholesky-vector counts (>= 1)                */
+    const double* L;       /* device [n_chol][v][v]                                             */
+    const double* t2;      /* device [o][o][v][v]                                               */
+    double* R;             /* device [o][o][v][v]; overwritten unless CC_FLAG_ACCUMULATE        */
+    double* energy;        /* nullable device scalar: E = sum_ijab (2 R_ijab - R_ijba) t2_ijab  */
+    int mode;              /* cc_precision                                                      */
+    int order;             /* cc_order                                                          */
+    int a_block;           /* 0 = planner's choice; else the number of `a` values per block     */
+    int flags;             /* cc_flags                                                          */
+    int slices;            /* Ozaki modes: BF16 slices per operand (0 = default 6; 2..8)         */
+    void* workspace;       /* device scratch, 256-byte aligned                                  */
+    size_t ws_bytes;       /* its size                                                          */
+    size_t budget_bytes;   /* workspace_size_ex only: upper bound for the plan (0 = 150 GB)     */
+    void* stream;          /* cudaStream_t                                                      */
+} cc_ladder_args;
+
+/* What the planner decided for a call (for reporting and tests). */
+typedef struct cc_ladder_plan {
+    int order;             /* CC_ORDER_INTEGRAL_FIRST or CC_ORDER_CHOLESKY_FIRST */
+    int a_block;           /* `a` values per block                               */
+    int n_blocks;          /* ceil(v / a_block)                                  */
+    int slices;            /* Ozaki slices (1 for the non-emulated modes)        */
+    int pairs;             /* GEMM rows used for (i,j): o*o, or o(o+1)/2 with symmetry */
+    size_t ws_bytes;       /* workspace the plan needs                           */
+    double flops_algorithmic; /* 2(o^2+n)v^4 (integral-first) or 4 n o^2 v^3     */
+    double flops_issued;      /* tensor-core flops actually issued (slice products, padding) */
+} cc_ladder_plan;
+
+/* Workspace bytes for cc_ladder_fwd with (mode, default order/flags) under `budget_bytes`
+ * (0 = 150 GB).  Writes *bytes.  CC_ERR_BUDGET if even one `a` per block does not fit. */
+int cc_ladder_workspace_size(int o, int v, int n_chol, int mode, size_t budget_bytes, size_t* bytes);
+
+/* Same for an explicit argument block (uses o, v, n_chol, mode, order, a_block, flags,
+ * slices, budget_bytes; pointers may be NULL). */
+int cc_ladder_workspace_size_ex(const cc_ladder_args* args, size_t* bytes);
+
+/* The plan cc_ladder_fwd_ex would run for `args` with its ws_bytes (pointers may be NULL). */
+int cc_ladder_plan_query(const cc_ladder_args* args, cc_ladder_plan* plan);
+
+/* R = sum_cd (ac|bd) t2_ijcd (Eq. 6) with default order (auto) and no flags.
+ * energy: nullable device scalar for E (see cc_ladder_args).  Returns cc_status. */
+int cc_ladder_fwd(int o, int v, int n_chol, const double* L, const double* t2, double* R, int mode,
+                  double* energy, void* workspace, size_t ws_bytes, void* stream);
+
+/* Forward with every option (order, a-block, accumulate, pair symmetry, exchange, slices). */
+int cc_ladder_fwd_ex(const cc_ladder_args* args);
+
+/* Workspace bytes for cc_ladder_bwd. */
+int cc_ladder_bwd_workspace_size(int o, int v, int n_chol, int mode, size_t budget_bytes, size_t* bytes);
+
+/* Adjoint of the forward for loss = sum W_ijab R_ijab, W = dR (device [o][o][v][v]):
+ *   dt2[i,j,c,d] = sum_ab W_ijab (ac|bd)                                 (nullable)
+ *   dL[P,e,f]    = sum_{ij,b,d} W_ijeb L_Pbd t_ijfd + sum_{ij,a,c} W_ijae L_Pac t_ijcf   (nullable)
+ * The (ac|bd) blocks are rebuilt (a-block recomputation), never stored whole.
+ * flags: CC_FLAG_SYMMETRIC_T lets dL use one pass with W + W^swap.  Overwrites dL / dt2. */
+int cc_ladder_bwd(int o, int v, int n_chol, const double* L, const double* t2, const double* dR,
+                  double* dL, double* dt2, int mode, void* workspace, size_t ws_bytes, void* stream);
+
+/* Adjoint with flags (CC_FLAG_SYMMETRIC_T, CC_FLAG_NO_STATUS_SYNC) and slices. */
+int cc_ladder_bwd_ex(int o, int v, int n_chol, const double* L, const double* t2, const double* dR,
+                     double* dL, double* dt2, int mode, int flags, int slices, void* workspace,
+                     size_t ws_bytes, void* stream);
+
+/* E = sum_ijab (2 R_ijab - R_ijba) t2_ijab into the device scalar `energy`, and, if e_pair is not
+ * NULL, e_pair[i*o+j] = the (i,j) part (device [o][o]).  Deterministic FP64 tree.
+ * Needs cc_ladder_energy_workspace_size() bytes of workspace. */
+int cc_ladder_energy(int o, int v, const double* R, const double* t2, double* energy, double* e_pair,
+                     void* workspace, size_t ws_bytes, void* stream);
+int cc_ladder_energy_workspace_size(int o, int v, size_t* bytes);
+
+/* Device status word of a workspace after calls made with CC_FLAG_NO_STATUS_SYNC
+ * (synchronises `stream`; returns CC_OK or CC_ERR_DEVICE_TIMEOUT and clears the word). */
+int cc_ladder_device_status(void* workspace, void* stream);
+
+/* Test knob: the bound, in nanoseconds, on every device-side wait (0 = library default of
+ * 2 s).  Applies to calls made after it on this process. */
+void cc_ladder_set_wait_limit_ns(unsigned long long ns);
+
+/* Building block used by every contraction above, exposed for direct use and testing:
+ *   C[m*ldc + n] (= or +=) sum_k A[m*lda + k] * B[n*ldb + k]     (row-major, K-contiguous FP64)
+ * in the arithmetic of `mode` (CC_FP64: DMMA; CC_OZAKI_BF16: split BF16 slices on tcgen05 with
+ * FP64 recombination; CC_TF32 / CC_BF16: one rounded copy, FP32 accumulation per K-chunk).
+ * accumulate != 0 adds into C.  Workspace from cc_ladder_gemm_workspace_size. */
+int cc_ladder_gemm_workspace_size(int mode, int M, int N, int K, int slices, size_t* bytes);
+int cc_ladder_gemm(int mode, int M, int N, int K, const double* A, int lda, const double* B, int ldb, double* C,
+                   int ldc, int accumulate, int slices, void* workspace, size_t ws_bytes, void* stream);
+
+/* Static description of a status code. */
+const char* cc_ladder_strerror(int status);
+
+/* Library version string. */
+const char* cc_ladder_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* CC_LADDER_H */

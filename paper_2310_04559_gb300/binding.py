@@ -1,0 +1,203 @@
+"""PyTorch-facing wrapper of the C ABI: workspace allocation, stream hand-off and
+a torch.autograd.Function for the ladder term
+
+    R[i,j,a,b] = sum_cd (sum_P L[P,a,c] L[P,b,d]) t2[i,j,c,d]      (Eq. 5 + Eq. 6)
+
+PyTorch provides device memory and the current stream only; the computation
+itself runs in libcc_ladder.so.
+"""
+from __future__ import annotations
+
+import ctypes
+
+import torch
+
+from . import _lib
+
+_MODE_ALIASES = {"ozaki": "ozaki_bf16", "emulated_fp64": "ozaki_bf16"}
+
+
+def _mode(m) -> int:
+    if isinstance(m, int):
+        return m
+    m = _MODE_ALIASES.get(m, m)
+    if m not in _lib.MODES:
+        raise ValueError(f"unknown mode {m!r}; one of {sorted(_lib.MODES)}")
+    return _lib.MODES[m]
+
+
+def _order(o) -> int:
+    if isinstance(o, int):
+        return o
+    if o not in _lib.ORDERS:
+        raise ValueError(f"unknown order {o!r}; one of {sorted(_lib.ORDERS)}")
+    return _lib.ORDERS[o]
+
+
+def _flags(symmetric=False, exchange=False, accumulate=False, no_sync=False) -> int:
+    return ((_lib.FLAG_SYMMETRIC_T if symmetric else 0) | (_lib.FLAG_EXCHANGE if exchange else 0)
+            | (_lib.FLAG_ACCUMULATE if accumulate else 0) | (_lib.FLAG_NO_STATUS_SYNC if no_sync else 0))
+
+
+def _check_tensor(x: torch.Tensor, name: str, shape):
+    if not isinstance(x, torch.Tensor):
+        raise TypeError(f"{name} must be a torch.Tensor")
+    if x.device.type != "cuda":
+        raise ValueError(f"{name} must be a CUDA tensor (no CPU path exists)")
+    if x.dtype != torch.float64:
+        raise TypeError(f"{name} must be float64")
+    if tuple(x.shape) != tuple(shape):
+        raise ValueError(f"{name} has shape {tuple(x.shape)}, expected {tuple(shape)}")
+    if not x.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+
+
+def _ptr(x):
+    return ctypes.c_void_p(x.data_ptr()) if x is not None else None
+
+
+def _stream(device=None):
+    return ctypes.c_void_p(torch.cuda.current_stream(device).cuda_stream)
+
+
+def _shapes(L, t2):
+    n, v, _ = L.shape
+    o = t2.shape[0]
+    return o, v, n
+
+
+def make_args(o, v, n, mode="fp64", order="auto", symmetric=False, exchange=False, accumulate=False,
+              a_block=0, slices=0, budget=0, no_sync=False) -> _lib.Args:
+    a = _lib.Args()
+    a.o, a.v, a.n_chol = o, v, n
+    a.mode, a.order = _mode(mode), _order(order)
+    a.a_block, a.slices = int(a_block), int(slices)
+    a.flags = _flags(symmetric, exchange, accumulate, no_sync)
+    a.budget_bytes = int(budget)
+    return a
+
+
+def workspace_size(o, v, n, **kw) -> int:
+    """Bytes of workspace the forward plan needs (keywords as in make_args)."""
+    lib = _lib.load()
+    a = make_args(o, v, n, **kw)
+    out = ctypes.c_size_t()
+    _lib.check(lib.cc_ladder_workspace_size_ex(ctypes.byref(a), ctypes.byref(out)), "cc_ladder_workspace_size_ex")
+    return out.value
+
+
+def plan(o, v, n, ws_bytes=0, **kw) -> dict:
+    lib = _lib.load()
+    a = make_args(o, v, n, **kw)
+    a.ws_bytes = int(ws_bytes)
+    p = _lib.Plan()
+    _lib.check(lib.cc_ladder_plan_query(ctypes.byref(a), ctypes.byref(p)), "cc_ladder_plan_query")
+    return {"order": {1: "integral_first", 2: "cholesky_first"}[p.order], "a_block": p.a_block,
+            "n_blocks": p.n_blocks, "slices": p.slices, "pairs": p.pairs, "ws_bytes": p.ws_bytes,
+            "flops_algorithmic": p.flops_algorithmic, "flops_issued": p.flops_issued}
+
+
+def alloc_workspace(nbytes: int, device) -> torch.Tensor:
+    return torch.empty(max(int(nbytes), 256), dtype=torch.uint8, device=device)
+
+
+def ladder_forward(L, t2, R=None, mode="ozaki_bf16", order="auto", symmetric=False, exchange=False,
+                   accumulate=False, a_block=0, slices=0, energy=False, workspace=None, budget=0, no_sync=False):
+    """R (new tensor unless given) and optionally the pair energy E (0-d tensor)."""
+    lib = _lib.load()
+    o, v, n = _shapes(L, t2)
+    _check_tensor(L, "L", (n, v, v))
+    _check_tensor(t2, "t2", (o, o, v, v))
+    if R is None:
+        R = torch.empty_like(t2) if not accumulate else torch.zeros_like(t2)
+    _check_tensor(R, "R", (o, o, v, v))
+    a = make_args(o, v, n, mode, order, symmetric, exchange, accumulate, a_block, slices, budget, no_sync)
+    if workspace is None:
+        ws = ctypes.c_size_t()
+        _lib.check(lib.cc_ladder_workspace_size_ex(ctypes.byref(a), ctypes.byref(ws)), "cc_ladder_workspace_size_ex")
+        workspace = alloc_workspace(ws.value, L.device)
+    E = torch.empty((), dtype=torch.float64, device=L.device) if energy else None
+    a.L, a.t2, a.R, a.energy = _ptr(L), _ptr(t2), _ptr(R), _ptr(E)
+    a.workspace, a.ws_bytes = _ptr(workspace), workspace.numel()
+    a.stream = _stream(L.device)
+    _lib.check(lib.cc_ladder_fwd_ex(ctypes.byref(a)), "cc_ladder_fwd_ex")
+    return (R, E) if energy else R
+
+
+def ladder_backward(L, t2, dR, mode="ozaki_bf16", symmetric=False, want_dL=True, want_dt2=True, slices=0,
+                    budget=0, workspace=None):
+    """Adjoint of the forward for loss = <dR, R>: returns (dL, dt2) (None where not wanted)."""
+    lib = _lib.load()
+    o, v, n = _shapes(L, t2)
+    _check_tensor(L, "L", (n, v, v))
+    _check_tensor(t2, "t2", (o, o, v, v))
+    _check_tensor(dR, "dR", (o, o, v, v))
+    if workspace is None:
+        ws = ctypes.c_size_t()
+        _lib.check(lib.cc_ladder_bwd_workspace_size(o, v, n, _mode(mode), int(budget), ctypes.byref(ws)),
+                   "cc_ladder_bwd_workspace_size")
+        workspace = alloc_workspace(ws.value, L.device)
+    dL = torch.empty_like(L) if want_dL else None
+    dt2 = torch.empty_like(t2) if want_dt2 else None
+    st = lib.cc_ladder_bwd_ex(o, v, n, _ptr(L), _ptr(t2), _ptr(dR), _ptr(dL), _ptr(dt2), _mode(mode),
+                              _flags(symmetric), int(slices), _ptr(workspace), workspace.numel(), _stream(L.device))
+    _lib.check(st, "cc_ladder_bwd_ex")
+    return dL, dt2
+
+
+def pair_energy(R, t2, pairs=False):
+    """E = sum_ijab (2 R_ijab - R_ijba) t2_ijab (and e_ij if pairs)."""
+    lib = _lib.load()
+    o, v = t2.shape[0], t2.shape[2]
+    _check_tensor(R, "R", (o, o, v, v))
+    _check_tensor(t2, "t2", (o, o, v, v))
+    ws = ctypes.c_size_t()
+    _lib.check(lib.cc_ladder_energy_workspace_size(o, v, ctypes.byref(ws)), "cc_ladder_energy_workspace_size")
+    w = alloc_workspace(ws.value, R.device)
+    E = torch.empty((), dtype=torch.float64, device=R.device)
+    ep = torch.empty((o, o), dtype=torch.float64, device=R.device) if pairs else None
+    _lib.check(lib.cc_ladder_energy(o, v, _ptr(R), _ptr(t2), _ptr(E), _ptr(ep), _ptr(w), w.numel(), _stream(R.device)),
+               "cc_ladder_energy")
+    return (E, ep) if pairs else E
+
+
+def gemm(A, B, mode="ozaki_bf16", C=None, accumulate=False, slices=0):
+    """C = A @ B.T (FP64 in and out) through the library's GEMM core in `mode`."""
+    lib = _lib.load()
+    M, K = A.shape
+    N = B.shape[0]
+    _check_tensor(A, "A", (M, K))
+    _check_tensor(B, "B", (N, K))
+    if C is None:
+        C = torch.zeros((M, N), dtype=torch.float64, device=A.device)
+    _check_tensor(C, "C", (M, N))
+    ws = ctypes.c_size_t()
+    _lib.check(lib.cc_ladder_gemm_workspace_size(_mode(mode), M, N, K, int(slices), ctypes.byref(ws)),
+               "cc_ladder_gemm_workspace_size")
+    w = alloc_workspace(ws.value, A.device)
+    _lib.check(lib.cc_ladder_gemm(_mode(mode), M, N, K, _ptr(A), K, _ptr(B), K, _ptr(C), N, int(accumulate),
+                                  int(slices), _ptr(w), w.numel(), _stream(A.device)), "cc_ladder_gemm")
+    return C
+
+
+class LadderFunction(torch.autograd.Function):
+    """R = ladder(L, t2) with the hand-written adjoint (integral blocks recomputed)."""
+
+    @staticmethod
+    def forward(ctx, L, t2, mode, order, symmetric, slices):
+        ctx.save_for_backward(L, t2)
+        ctx.mode, ctx.symmetric, ctx.slices = mode, symmetric, slices
+        return ladder_forward(L, t2, mode=mode, order=order, symmetric=symmetric, slices=slices)
+
+    @staticmethod
+    def backward(ctx, dR):
+        L, t2 = ctx.saved_tensors
+        dL, dt2 = ladder_backward(L, t2, dR.contiguous(), mode=ctx.mode, symmetric=ctx.symmetric,
+                                  want_dL=ctx.needs_input_grad[0], want_dt2=ctx.needs_input_grad[1],
+                                  slices=ctx.slices)
+        return dL, dt2, None, None, None, None
+
+
+def ladder(L, t2, mode="ozaki_bf16", order="auto", symmetric=False, slices=0):
+    """Differentiable ladder term R[i,j,a,b] = sum_cd (ac|bd) t2[i,j,c,d]."""
+    return LadderFunction.apply(L, t2, mode, order, symmetric, slices)

@@ -1,0 +1,763 @@
+// api.cu -- the C ABI of include/cc_ladder.h: argument validation, the planner
+// (contraction order, block of `a` values, workspace carve), and the sequence of
+// device steps for the forward, the adjoint and the pair energy.
+//
+// Forward, integral-first order (Section 3.2, the for-loop over `a` widened to
+// blocks of A values):
+//   for each block a0 .. a0+A-1:
+//     KG1  V[a,b,c,d] = sum_P L[P,a,c] L[P,b,d]              (Eq. 5; GEMM M=A*v, N=v^2, K=n)
+//     KG2  R[ij,a,b]  = sum_(c,d) t2[ij,c,d] V[a,b,c,d]       (Eq. 6; GEMM M=o^2, N=A*v, K=v^2)
+// Forward, Cholesky-first order (Section 3.2, the L.t intermediate):
+//     CF1  X[ij,a,P,d] = sum_c L[P,a,c] t2[ij,c,d]            (GEMM M=A*n, N=o^2*v, K=v)
+//     CF2  R[ij,a,b]   = sum_(P,d) X[ij,a,P,d] L[P,b,d]        (GEMM M=o^2*A, N=v, K=n*v)
+// In the emulated-FP64 and mixed modes every GEMM operand is first turned into
+// a slice stack (split.cu) and the GEMM runs on the tensor cores (gemm_tc.cu);
+// in the FP64 mode the GEMMs run on DMMA (gemm_f64.cu) straight from FP64.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <atomic>
+#include <cmath>
+#include <cstdint>
+#include <cstring>
+#include <mutex>
+
+#include "cc_internal.cuh"
+
+using namespace cc;
+
+namespace {
+
+constexpr int kDefaultSlices = 6;
+constexpr int kBeta = 7;                 // bits per Ozaki slice (balanced digits in [-64, 64])
+constexpr int kMixedChunk = 16384;       // K elements per FP32 accumulation in the BF16 / TF32 modes
+constexpr size_t kDefaultBudget = 150ull << 30;
+
+std::atomic<unsigned long long> g_wait_ns{2000000000ull};
+
+inline size_t al256(size_t x) { return (x + 255) & ~(size_t)255; }
+inline long long pitch_for(long long K, int esz) { const long long q = 16 / esz; return (K + q - 1) / q * q; }
+
+struct Carve {
+    size_t cur = 0;
+    size_t take(size_t bytes)
+    {
+        const size_t o = cur;
+        cur = al256(cur + bytes);
+        return o;
+    }
+};
+
+bool is_tc(int mode) { return mode == CC_OZAKI_BF16 || mode == CC_BF16 || mode == CC_TF32; }
+int esz_of(int mode) { return mode == CC_TF32 ? 4 : 2; }
+int slices_of(int mode, int slices) { return mode == CC_OZAKI_BF16 ? (slices > 0 ? slices : kDefaultSlices) : 1; }
+
+struct Ctx {
+    int o, v, n;
+    int mode, order, flags, s;
+    bool sym, exch;
+    long long pairs;  // GEMM rows for (i,j)
+};
+
+// ------------------------------------------------------------------ workspace
+struct FwdLayout {
+    size_t status, pairtab, t2x, Rc, epart, epair;
+    // integral-first
+    size_t V, Lw, eL, colmax, tw, et, Vw, eV;
+    // Cholesky-first
+    size_t X2, LwA, eLA, twB, etB, X2w, eX2, LwB, eLB;
+    size_t total;
+};
+
+FwdLayout layout_fwd(const Ctx& c, int A)
+{
+    FwdLayout L{};
+    Carve cv;
+    const long long o = c.o, v = c.v, n = c.n, vv = v * v, P = c.pairs;
+    L.status = cv.take(256);
+    if (c.sym) L.pairtab = cv.take(8 * P);
+    if (c.exch) L.t2x = cv.take(8 * o * o * vv);
+    if (c.sym) L.Rc = cv.take(8 * P * vv);
+    L.epart = cv.take(8 * energy_scratch_doubles(c.o, c.v));
+    L.epair = cv.take(8 * o * o);
+    const int es = esz_of(c.mode);
+    const long long s = c.s;
+    if (c.order == CC_ORDER_INTEGRAL_FIRST) {
+        L.V = cv.take(8 * (long long)A * v * vv);
+        if (is_tc(c.mode)) {
+            L.Lw = cv.take(es * s * vv * pitch_for(n, es));
+            L.eL = cv.take(4 * vv);
+            L.colmax = cv.take(8 * vv);
+            L.tw = cv.take(es * s * P * pitch_for(vv, es));
+            L.et = cv.take(4 * P);
+            L.Vw = cv.take(es * s * (long long)A * v * pitch_for(vv, es));
+            L.eV = cv.take(4 * (long long)A * v);
+        }
+    } else {
+        L.X2 = cv.take(8 * P * (long long)A * n * v);
+        if (is_tc(c.mode)) {
+            L.LwA = cv.take(es * s * v * n * pitch_for(v, es));
+            L.eLA = cv.take(4 * v * n);
+            L.twB = cv.take(es * s * P * v * pitch_for(v, es));
+            L.etB = cv.take(4 * P * v);
+            L.colmax = cv.take(8 * P * v);
+            L.X2w = cv.take(es * s * P * (long long)A * pitch_for(n * v, es));
+            L.eX2 = cv.take(4 * P * (long long)A);
+            L.LwB = cv.take(es * s * v * pitch_for(n * v, es));
+            L.eLB = cv.take(4 * v);
+        }
+    }
+    L.total = cv.cur;
+    return L;
+}
+
+struct BwdLayout {
+    size_t status, LT, Wx, tx, M1, fwd;  // fwd = nested forward workspace for dt2
+    size_t Lw, eL, Ww, eW, tw, et, colmax, M1w, eM1;
+    size_t total;
+};
+
+// ------------------------------------------------------------------ planner
+double flops_if(const Ctx& c) { return 2.0 * ((double)c.pairs + c.n) * std::pow((double)c.v, 4); }
+double flops_cf(const Ctx& c) { return 4.0 * c.n * (double)c.pairs * std::pow((double)c.v, 3); }
+
+int pick_order(const Ctx& c, int requested)
+{
+    if (requested == CC_ORDER_INTEGRAL_FIRST || requested == CC_ORDER_CHOLESKY_FIRST) return requested;
+    // Cost model: tensor-core flops, with the Cholesky-first order charged for its
+    // larger intermediate traffic (it writes and re-reads o^2 n v^2 per block).
+    const double cf = flops_cf(c) * 1.15, itf = flops_if(c);
+    return cf < itf ? CC_ORDER_CHOLESKY_FIRST : CC_ORDER_INTEGRAL_FIRST;
+}
+
+// Largest block fitting `bytes`, then evened out over the blocks it implies.
+int pick_block(const Ctx& c, size_t bytes, int requested, size_t* need)
+{
+    if (requested > 0) {
+        const int A = std::min(requested, c.v);
+        *need = layout_fwd(c, A).total;
+        return *need <= bytes ? A : -1;
+    }
+    if (layout_fwd(c, 1).total > bytes) { *need = layout_fwd(c, 1).total; return -1; }
+    int lo = 1, hi = c.v;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) / 2;
+        if (layout_fwd(c, mid).total <= bytes) lo = mid; else hi = mid - 1;
+    }
+    const int nb = (c.v + lo - 1) / lo;
+    const int A = (c.v + nb - 1) / nb;
+    *need = layout_fwd(c, A).total;
+    return A;
+}
+
+int make_ctx(const cc_ladder_args* a, Ctx* c)
+{
+    if (!a) return CC_ERR_NULL;
+    if (a->o < 1 || a->v < 1 || a->n_chol < 1) return CC_ERR_SHAPE;
+    if ((double)a->o * a->o * a->v * a->v > 4.0e12 || (double)a->n_chol * a->v * a->v > 4.0e12) return CC_ERR_SHAPE;
+    if (a->v > 46340 || a->o > 46340) return CC_ERR_SHAPE;
+    if (a->mode == CC_OZAKI_INT8) return CC_ERR_UNSUPPORTED;
+    if (a->mode < CC_FP64 || a->mode > CC_BF16) return CC_ERR_ARG;
+    if (a->order < CC_ORDER_AUTO || a->order > CC_ORDER_CHOLESKY_FIRST) return CC_ERR_ARG;
+    if (a->a_block < 0) return CC_ERR_ARG;
+    if (a->flags & ~(CC_FLAG_ACCUMULATE | CC_FLAG_SYMMETRIC_T | CC_FLAG_EXCHANGE | CC_FLAG_NO_STATUS_SYNC)) return CC_ERR_ARG;
+    if (a->mode == CC_OZAKI_BF16 && a->slices != 0 && (a->slices < 2 || a->slices > 8)) return CC_ERR_ARG;
+    c->o = a->o; c->v = a->v; c->n = a->n_chol;
+    c->mode = a->mode; c->flags = a->flags;
+    c->s = slices_of(a->mode, a->slices);
+    c->sym = (a->flags & CC_FLAG_SYMMETRIC_T) != 0;
+    c->exch = (a->flags & CC_FLAG_EXCHANGE) != 0;
+    c->pairs = c->sym ? (long long)a->o * (a->o + 1) / 2 : (long long)a->o * a->o;
+    c->order = pick_order(*c, a->order);
+    return CC_OK;
+}
+
+bool aligned(const void* p, size_t al) { return ((uintptr_t)p % al) == 0; }
+
+int check_cuda(cudaError_t e) { return e == cudaSuccess ? CC_OK : CC_ERR_CUDA; }
+
+#define CC_TRY(x)                      \
+    do {                               \
+        const int _st = (x);           \
+        if (_st != CC_OK) return _st;  \
+    } while (0)
+#define CC_CU(x) CC_TRY(check_cuda(x))
+
+int finish(void* ws_status, int flags, cudaStream_t s)
+{
+    CC_CU(cudaGetLastError());
+    if (flags & CC_FLAG_NO_STATUS_SYNC) return CC_OK;
+    CC_CU(cudaStreamSynchronize(s));
+    int h = 0;
+    CC_CU(cudaMemcpy(&h, ws_status, sizeof(int), cudaMemcpyDeviceToHost));
+    return h ? CC_ERR_DEVICE_TIMEOUT : CC_OK;
+}
+
+// ---------------------------------------------------- tensor-core operand prep
+struct Operand {
+    void* D; int* e; long long pitch, rows;
+};
+
+int prep_rows(const Ctx& c, const RowSrc& src, Operand& op, cudaStream_t st)
+{
+    op.rows = src.rows;
+    op.pitch = pitch_for(src.K, esz_of(c.mode));
+    if (c.mode == CC_TF32) return check_cuda(convert_rows_tf32(src, (float*)op.D, op.pitch, st));
+    const int s = c.mode == CC_OZAKI_BF16 ? c.s : 0;
+    return check_cuda(split_rows_bf16(src, s, kBeta, op.D, op.pitch, op.e, st));
+}
+
+int prep_cols(const Ctx& c, const ColSrc& src, Operand& op, unsigned long long* colmax, cudaStream_t st)
+{
+    op.rows = src.rows;
+    op.pitch = pitch_for(src.K, esz_of(c.mode));
+    if (c.mode == CC_TF32) return check_cuda(convert_cols_tf32(src, (float*)op.D, op.pitch, st));
+    const int s = c.mode == CC_OZAKI_BF16 ? c.s : 0;
+    return check_cuda(split_cols_bf16(src, s, kBeta, op.D, op.pitch, op.e, colmax, st));
+}
+
+int run_tc(const Ctx& c, int M, int N, int K, const Operand& A, long long rowA0, const Operand& B, long long rowB0,
+           const OutDesc& out, int* status, cudaStream_t st)
+{
+    GemmTc g{};
+    g.kind = c.mode == CC_TF32 ? TC_TF32 : TC_BF16;
+    g.M = M; g.N = N; g.K = K;
+    g.A = A.D; g.pitchA = A.pitch; g.rowsA = A.rows; g.rowA0 = rowA0;
+    g.B = B.D; g.pitchB = B.pitch; g.rowsB = B.rows; g.rowB0 = rowB0;
+    g.slices = c.s;
+    g.eA = c.mode == CC_TF32 ? nullptr : A.e;
+    g.eB = c.mode == CC_TF32 ? nullptr : B.e;
+    g.beta = kBeta;
+    g.scale_base = c.mode == CC_OZAKI_BF16 ? 2 - 2 * kBeta : 0;
+    g.level0 = 0;
+    g.nlevel = c.mode == CC_OZAKI_BF16 ? c.s : 1;
+    for (int i = 0; i < g.nlevel; ++i) g.kchunk[i] = c.mode == CC_OZAKI_BF16 ? 0 : kMixedChunk;
+    g.out = out;
+    g.status = status;
+    g.wait_ns = g_wait_ns.load();
+    return check_cuda(gemm_tc(g, st));
+}
+
+template <typename T>
+T* at(void* ws, size_t off) { return (T*)((char*)ws + off); }
+
+// ----------------------------------------------------------------- forward
+int fwd_impl(const cc_ladder_args* a, const double* Lsrc_override = nullptr)
+{
+    Ctx c;
+    CC_TRY(make_ctx(a, &c));
+    const double* Lsrc = Lsrc_override ? Lsrc_override : a->L;
+    if (!Lsrc || !a->t2 || !a->R || !a->workspace) return CC_ERR_NULL;
+    if (!aligned(Lsrc, 16) || !aligned(a->t2, 16) || !aligned(a->R, 16) || !aligned(a->workspace, 256) ||
+        (a->energy && !aligned(a->energy, 8)))
+        return CC_ERR_ALIGN;
+    if (is_tc(c.mode) && !tc_gemm_available()) return CC_ERR_UNSUPPORTED;
+    size_t need = 0;
+    const int A = pick_block(c, a->ws_bytes, a->a_block, &need);
+    if (A < 0) return CC_ERR_WORKSPACE;
+    const FwdLayout Lo = layout_fwd(c, A);
+    void* ws = a->workspace;
+    cudaStream_t st = (cudaStream_t)a->stream;
+    const long long o = c.o, v = c.v, n = c.n, vv = v * v;
+    int* status = at<int>(ws, Lo.status);
+    CC_CU(cudaMemsetAsync(status, 0, 256, st));
+
+    const double* t2 = a->t2;
+    if (c.exch) {  // Eq. 7 = Eq. 6 applied to t2 with c <-> d swapped
+        CC_CU(swap_last2(o * o, c.v, a->t2, at<double>(ws, Lo.t2x), st));
+        t2 = at<double>(ws, Lo.t2x);
+    }
+    long long* pairtab = c.sym ? at<long long>(ws, Lo.pairtab) : nullptr;
+    if (c.sym) CC_CU(fill_pair_table(c.o, c.v, pairtab, st));
+    // rows of t2 used as GEMM rows: all (i,j), or the pairs i <= j
+    const Map2 trows = c.sym ? table_map(pairtab) : plain_map(vv);
+    double* Rdst = c.sym ? at<double>(ws, Lo.Rc) : a->R;
+    const int accum = (!c.sym && (c.flags & CC_FLAG_ACCUMULATE)) ? 1 : 0;
+
+    if (c.order == CC_ORDER_INTEGRAL_FIRST) {
+        double* V = at<double>(ws, Lo.V);
+        Operand Lw{}, tw{}, Vw{};
+        if (is_tc(c.mode)) {
+            Lw.D = at<void>(ws, Lo.Lw); Lw.e = at<int>(ws, Lo.eL);
+            tw.D = at<void>(ws, Lo.tw); tw.e = at<int>(ws, Lo.et);
+            Vw.D = at<void>(ws, Lo.Vw); Vw.e = at<int>(ws, Lo.eV);
+            // L rows (a,c) are contiguous in L[P][a][c]; K = P is strided
+            ColSrc ls{Lsrc, vv, vv, n, 0, plain_map(0)};
+            CC_TRY(prep_cols(c, ls, Lw, at<unsigned long long>(ws, Lo.colmax), st));
+            RowSrc ts{t2, trows, plain_map(1), c.pairs, vv};
+            CC_TRY(prep_rows(c, ts, tw, st));
+        }
+        for (int a0 = 0; a0 < c.v; a0 += A) {
+            const int Ab = std::min(A, c.v - a0);
+            // KG1: V[al][b][c][d], GEMM rows (al,c), cols (b,d)
+            OutDesc o1{V, split_map(v, v * vv, v), split_map(v, vv, 1), 0};
+            if (c.mode == CC_FP64) {
+                GemmF64 g{};
+                g.M = Ab * c.v; g.N = (int)vv; g.K = c.n;
+                g.A = Lsrc; g.am = plain_map(1, (long long)a0 * v); g.ak = plain_map(vv);
+                g.B = Lsrc; g.bm = plain_map(1); g.bk = plain_map(vv);
+                g.out = o1;
+                CC_CU(gemm_f64(g, st));
+            } else {
+                CC_TRY(run_tc(c, Ab * c.v, (int)vv, c.n, Lw, (long long)a0 * v, Lw, 0, o1, status, st));
+            }
+            // KG2: R[ij][a0+al][b] = sum_(c,d) t2[ij][(c,d)] V[al][b][(c,d)]
+            OutDesc o2{Rdst, plain_map(vv), plain_map(1, (long long)a0 * v), accum};
+            if (c.mode == CC_FP64) {
+                GemmF64 g{};
+                g.M = (int)c.pairs; g.N = Ab * c.v; g.K = (int)vv;
+                g.A = t2; g.am = trows; g.ak = plain_map(1);
+                g.B = V; g.bm = plain_map(vv); g.bk = plain_map(1);
+                g.out = o2;
+                CC_CU(gemm_f64(g, st));
+            } else {
+                RowSrc vs{V, plain_map(vv), plain_map(1), (long long)Ab * v, vv};
+                CC_TRY(prep_rows(c, vs, Vw, st));
+                CC_TRY(run_tc(c, (int)c.pairs, Ab * c.v, (int)vv, tw, 0, Vw, 0, o2, status, st));
+            }
+        }
+    } else {
+        // Cholesky-first.  Rows of CF1's B operand are (p, d): t2 rows p, element c*v + d.
+        double* X2 = at<double>(ws, Lo.X2);
+        Operand LwA{}, twB{}, X2w{}, LwB{};
+        if (is_tc(c.mode)) {
+            LwA.D = at<void>(ws, Lo.LwA); LwA.e = at<int>(ws, Lo.eLA);
+            twB.D = at<void>(ws, Lo.twB); twB.e = at<int>(ws, Lo.etB);
+            X2w.D = at<void>(ws, Lo.X2w); X2w.e = at<int>(ws, Lo.eX2);
+            LwB.D = at<void>(ws, Lo.LwB); LwB.e = at<int>(ws, Lo.eLB);
+            // CF1 A: rows (a, P) over all a, K = c contiguous: L[P][a][c]
+            RowSrc la{Lsrc, split_map(n, v, vv), plain_map(1), v * n, v};
+            CC_TRY(prep_rows(c, la, LwA, st));
+            // CF1 B: rows (p, d), K = c: batched, rows d contiguous within t2[p]
+            ColSrc tb{t2, v, c.pairs * v, v, v, c.sym ? table_map(pairtab) : plain_map(vv)};
+            CC_TRY(prep_cols(c, tb, twB, at<unsigned long long>(ws, Lo.colmax), st));
+            // CF2 B: rows b, K = (P, d): L[P][b][d]
+            RowSrc lb{Lsrc, plain_map(v), split_map(v, vv, 1), v, n * v};
+            CC_TRY(prep_rows(c, lb, LwB, st));
+        }
+        for (int a0 = 0; a0 < c.v; a0 += A) {
+            const int Ab = std::min(A, c.v - a0);
+            // CF1: rows (al, P), cols (p, d), K = c  ->  X2[(p, al), (P, d)]
+            OutDesc o1{X2, split_map(n, n * v, v), split_map(v, (long long)Ab * n * v, 1), 0};
+            if (c.mode == CC_FP64) {
+                GemmF64 g{};
+                g.M = Ab * c.n; g.N = (int)(c.pairs * v); g.K = c.v;
+                g.A = Lsrc; g.am = split_map(n, v, vv, (long long)a0 * v); g.ak = plain_map(1);
+                g.B = t2; g.bm = c.sym ? table_map(pairtab, v, 1) : split_map(v, vv, 1); g.bk = plain_map(v);
+                g.out = o1;
+                CC_CU(gemm_f64(g, st));
+            } else {
+                CC_TRY(run_tc(c, Ab * c.n, (int)(c.pairs * v), c.v, LwA, (long long)a0 * n, twB, 0, o1, status, st));
+            }
+            // CF2: rows (p, al), cols b, K = (P, d)  ->  R[p][a0+al][b]
+            OutDesc o2{Rdst, split_map(Ab, vv, v, (long long)a0 * v), plain_map(1), accum};
+            if (c.mode == CC_FP64) {
+                GemmF64 g{};
+                g.M = (int)(c.pairs * Ab); g.N = c.v; g.K = (int)(n * v);
+                g.A = X2; g.am = plain_map(n * v); g.ak = plain_map(1);
+                g.B = Lsrc; g.bm = plain_map(v); g.bk = split_map(v, vv, 1);
+                g.out = o2;
+                if (c.sym) g.out.rmap = split_map(Ab, vv, v, (long long)a0 * v);
+                CC_CU(gemm_f64(g, st));
+            } else {
+                RowSrc xs{X2, plain_map(n * v), plain_map(1), c.pairs * Ab, n * v};
+                CC_TRY(prep_rows(c, xs, X2w, st));
+                CC_TRY(run_tc(c, (int)(c.pairs * Ab), c.v, (int)(n * v), X2w, 0, LwB, 0, o2, status, st));
+            }
+        }
+    }
+    if (c.sym) CC_CU(scatter_pairs(c.o, c.v, at<double>(ws, Lo.Rc), a->R, (c.flags & CC_FLAG_ACCUMULATE) ? 1 : 0, st));
+    if (a->energy) {
+        CC_CU(energy_pairs(c.o, c.v, a->R, a->t2, at<double>(ws, Lo.epart), at<double>(ws, Lo.epair), st));
+        CC_CU(energy_total(c.o * c.o, at<double>(ws, Lo.epair), a->energy, st));
+    }
+    return finish(status, c.flags, st);
+}
+
+// ----------------------------------------------------------------- adjoint
+// dt2 = forward with L'[P,a,c] = L[P,c,a] applied to W (integral symmetry (ac|bd)).
+// dL  = T1[W, t] + T1[W^swap, t^swap], T1[X,t][P,e,f] = sum_(b,d) L[P,b,d] M1[e,f,b,d],
+//       M1[e,f,b,d] = sum_ij X[ij,e,b] t[ij,f,d]; for pair-symmetric t this is T1[W + W^swap, t].
+struct BwdPlan {
+    Ctx c;      // c.pairs = o*o (W has no pair symmetry)
+    int E;      // e-block for M1
+    cc_ladder_args fa;  // nested forward for dt2
+    size_t fwd_bytes;
+    BwdLayout L;
+};
+
+BwdLayout layout_bwd(const Ctx& c, int E, size_t fwd_bytes, bool sym)
+{
+    BwdLayout L{};
+    Carve cv;
+    const long long o = c.o, v = c.v, n = c.n, vv = v * v, P = (long long)o * o;
+    L.status = cv.take(256);
+    L.LT = cv.take(8 * n * vv);
+    L.Wx = cv.take(8 * P * vv);
+    if (!sym) L.tx = cv.take(8 * P * vv);
+    L.M1 = cv.take(8 * (long long)E * v * vv);
+    if (is_tc(c.mode)) {
+        const int es = esz_of(c.mode);
+        const long long s = c.s;
+        L.Lw = cv.take(es * s * n * pitch_for(vv, es));
+        L.eL = cv.take(4 * n);
+        L.Ww = cv.take(es * s * (long long)E * v * pitch_for(P, es));
+        L.eW = cv.take(4 * (long long)E * v);
+        L.tw = cv.take(es * s * vv * pitch_for(P, es));
+        L.et = cv.take(4 * vv);
+        L.colmax = cv.take(8 * vv);
+        L.M1w = cv.take(es * s * (long long)E * v * pitch_for(vv, es));
+        L.eM1 = cv.take(4 * (long long)E * v);
+    }
+    L.fwd = cv.take(fwd_bytes);
+    L.total = cv.cur;
+    return L;
+}
+
+int bwd_plan(int o, int v, int n, int mode, int flags, int slices, size_t bytes, bool for_query, BwdPlan* bp)
+{
+    cc_ladder_args fa{};
+    fa.o = o; fa.v = v; fa.n_chol = n; fa.mode = mode; fa.order = CC_ORDER_INTEGRAL_FIRST; fa.slices = slices;
+    fa.flags = flags & CC_FLAG_NO_STATUS_SYNC;
+    Ctx c;
+    CC_TRY(make_ctx(&fa, &c));
+    const bool sym = (flags & CC_FLAG_SYMMETRIC_T) != 0;
+    // Split the budget: find the largest block E (used for both the nested forward's
+    // integral block and the M1 block) such that everything fits.
+    auto total_for = [&](int A) {
+        const size_t fb = layout_fwd(c, A).total;
+        return layout_bwd(c, A, fb, sym).total;
+    };
+    if (total_for(1) > bytes) return for_query ? CC_ERR_BUDGET : CC_ERR_WORKSPACE;
+    int lo = 1, hi = v;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) / 2;
+        if (total_for(mid) <= bytes) lo = mid; else hi = mid - 1;
+    }
+    const int nb = (v + lo - 1) / lo;
+    const int A = (v + nb - 1) / nb;
+    bp->c = c;
+    bp->E = A;
+    bp->fwd_bytes = layout_fwd(c, A).total;
+    bp->L = layout_bwd(c, A, bp->fwd_bytes, sym);
+    bp->fa = fa;
+    bp->fa.a_block = A;
+    return CC_OK;
+}
+
+int bwd_impl(int o, int v, int n, const double* L, const double* t2, const double* W, double* dL, double* dt2, int mode,
+             int flags, int slices, void* ws, size_t ws_bytes, void* stream)
+{
+    if (flags & ~(CC_FLAG_SYMMETRIC_T | CC_FLAG_NO_STATUS_SYNC)) return CC_ERR_ARG;
+    BwdPlan bp;
+    {
+        cc_ladder_args probe{};
+        probe.o = o; probe.v = v; probe.n_chol = n; probe.mode = mode; probe.slices = slices;
+        Ctx tmp;
+        CC_TRY(make_ctx(&probe, &tmp));
+    }
+    if (!L || !t2 || !W || !ws) return CC_ERR_NULL;
+    if (!aligned(L, 16) || !aligned(t2, 16) || !aligned(W, 16) || !aligned(ws, 256) || (dL && !aligned(dL, 16)) ||
+        (dt2 && !aligned(dt2, 16)))
+        return CC_ERR_ALIGN;
+    CC_TRY(bwd_plan(o, v, n, mode, flags, slices, ws_bytes, false, &bp));
+    if (is_tc(mode) && !tc_gemm_available()) return CC_ERR_UNSUPPORTED;
+    const Ctx& c = bp.c;
+    const BwdLayout& Lo = bp.L;
+    cudaStream_t st = (cudaStream_t)stream;
+    const long long vv = (long long)v * v, P = (long long)o * o;
+    int* status = at<int>(ws, Lo.status);
+    CC_CU(cudaMemsetAsync(status, 0, 256, st));
+    const bool sym = (flags & CC_FLAG_SYMMETRIC_T) != 0;
+
+    if (dt2) {
+        double* LT = at<double>(ws, Lo.LT);
+        CC_CU(transpose_last2(n, v, L, LT, st));
+        cc_ladder_args fa = bp.fa;
+        fa.L = LT; fa.t2 = W; fa.R = dt2; fa.energy = nullptr;
+        fa.workspace = at<void>(ws, Lo.fwd); fa.ws_bytes = bp.fwd_bytes;
+        fa.stream = stream;
+        fa.flags = CC_FLAG_NO_STATUS_SYNC;
+        CC_TRY(fwd_impl(&fa));
+        // the nested call has its own status word; fold it into ours
+        int* st2 = at<int>(fa.workspace, 0);
+        CC_CU(cudaMemcpyAsync(status + 1, st2, sizeof(int), cudaMemcpyDeviceToDevice, st));
+    }
+    if (dL) {
+        double* Wx = at<double>(ws, Lo.Wx);
+        const double* tt[2];
+        const double* Xs[2];
+        int npass;
+        if (sym) {
+            CC_CU(add_pair_swap(o, v, W, Wx, 1, st));  // W + W^swap
+            Xs[0] = Wx; tt[0] = t2; npass = 1;
+        } else {
+            double* tx = at<double>(ws, Lo.tx);
+            CC_CU(add_pair_swap(o, v, W, Wx, 0, st));   // W^swap
+            CC_CU(add_pair_swap(o, v, t2, tx, 0, st));  // t^swap
+            Xs[0] = W; tt[0] = t2; Xs[1] = Wx; tt[1] = tx; npass = 2;
+        }
+        double* M1 = at<double>(ws, Lo.M1);
+        const int E = bp.E;
+        Operand Lw{}, Ww{}, tw{}, M1w{};
+        if (is_tc(mode)) {
+            Lw.D = at<void>(ws, Lo.Lw); Lw.e = at<int>(ws, Lo.eL);
+            Ww.D = at<void>(ws, Lo.Ww); Ww.e = at<int>(ws, Lo.eW);
+            tw.D = at<void>(ws, Lo.tw); tw.e = at<int>(ws, Lo.et);
+            M1w.D = at<void>(ws, Lo.M1w); M1w.e = at<int>(ws, Lo.eM1);
+            RowSrc ls{L, plain_map(vv), plain_map(1), n, vv};  // T1 A: rows P, K = (b,d)
+            CC_TRY(prep_rows(c, ls, Lw, st));
+        }
+        for (int pass = 0; pass < npass; ++pass) {
+            if (is_tc(mode)) {
+                ColSrc ts{tt[pass], vv, vv, P, 0, plain_map(0)};  // M1 B: rows (f,d), K = ij
+                CC_TRY(prep_cols(c, ts, tw, at<unsigned long long>(ws, Lo.colmax), st));
+            }
+            for (int e0 = 0; e0 < v; e0 += E) {
+                const int Eb = std::min(E, v - e0);
+                // M1: rows (el,b), cols (f,d), K = ij  ->  M1[el][f][b][d]
+                OutDesc o1{M1, split_map(v, v * vv, v), split_map(v, vv, 1), 0};
+                if (mode == CC_FP64) {
+                    GemmF64 g{};
+                    g.M = Eb * v; g.N = (int)vv; g.K = (int)P;
+                    g.A = Xs[pass]; g.am = plain_map(1, (long long)e0 * v); g.ak = plain_map(vv);
+                    g.B = tt[pass]; g.bm = plain_map(1); g.bk = plain_map(vv);
+                    g.out = o1;
+                    CC_CU(gemm_f64(g, st));
+                } else {
+                    ColSrc ws_{Xs[pass] + (long long)e0 * v, vv, (long long)Eb * v, P, 0, plain_map(0)};
+                    CC_TRY(prep_cols(c, ws_, Ww, at<unsigned long long>(ws, Lo.colmax), st));
+                    CC_TRY(run_tc(c, Eb * v, (int)vv, (int)P, Ww, 0, tw, 0, o1, status, st));
+                }
+                // T1: dL[P][e0+el][f] (+)= sum_(b,d) L[P][(b,d)] M1[(el,f)][(b,d)]
+                OutDesc o2{dL, plain_map(vv), plain_map(1, (long long)e0 * v), pass > 0 ? 1 : 0};
+                if (mode == CC_FP64) {
+                    GemmF64 g{};
+                    g.M = n; g.N = Eb * v; g.K = (int)vv;
+                    g.A = L; g.am = plain_map(vv); g.ak = plain_map(1);
+                    g.B = M1; g.bm = plain_map(vv); g.bk = plain_map(1);
+                    g.out = o2;
+                    CC_CU(gemm_f64(g, st));
+                } else {
+                    RowSrc ms{M1, plain_map(vv), plain_map(1), (long long)Eb * v, vv};
+                    CC_TRY(prep_rows(c, ms, M1w, st));
+                    CC_TRY(run_tc(c, n, Eb * v, (int)vv, Lw, 0, M1w, 0, o2, status, st));
+                }
+            }
+        }
+    }
+    CC_CU(cudaGetLastError());
+    if (flags & CC_FLAG_NO_STATUS_SYNC) return CC_OK;
+    CC_CU(cudaStreamSynchronize(st));
+    int h[2] = {0, 0};
+    CC_CU(cudaMemcpy(h, status, sizeof(h), cudaMemcpyDeviceToHost));
+    return (h[0] | h[1]) ? CC_ERR_DEVICE_TIMEOUT : CC_OK;
+}
+
+}  // namespace
+
+// ======================================================================= ABI
+extern "C" {
+
+const char* cc_ladder_strerror(int status)
+{
+    switch (status) {
+    case CC_OK: return "ok";
+    case CC_ERR_SHAPE: return "invalid shape (o, v, n_chol must be >= 1 and not overflow)";
+    case CC_ERR_NULL: return "required pointer is NULL";
+    case CC_ERR_ALIGN: return "pointer misaligned (tensors 16 bytes, workspace 256 bytes)";
+    case CC_ERR_WORKSPACE: return "workspace smaller than the plan needs";
+    case CC_ERR_BUDGET: return "budget below the smallest plan";
+    case CC_ERR_UNSUPPORTED: return "mode/order/flag combination not supported on this device";
+    case CC_ERR_CUDA: return "CUDA runtime error";
+    case CC_ERR_DEVICE_TIMEOUT: return "a bounded device-side wait expired; results are invalid";
+    case CC_ERR_ARG: return "invalid argument";
+    default: return "unknown status";
+    }
+}
+
+const char* cc_ladder_version(void) { return "cc_ladder 0.1 (sm_103a)"; }
+
+void cc_ladder_set_wait_limit_ns(unsigned long long ns) { g_wait_ns.store(ns ? ns : 2000000000ull); }
+
+int cc_ladder_workspace_size_ex(const cc_ladder_args* args, size_t* bytes)
+{
+    if (!bytes) return CC_ERR_NULL;
+    Ctx c;
+    CC_TRY(make_ctx(args, &c));
+    const size_t budget = args->budget_bytes ? args->budget_bytes : kDefaultBudget;
+    size_t need = 0;
+    const int A = pick_block(c, budget, args->a_block, &need);
+    if (A < 0) return args->a_block > 0 ? CC_ERR_BUDGET : CC_ERR_BUDGET;
+    *bytes = need;
+    return CC_OK;
+}
+
+int cc_ladder_workspace_size(int o, int v, int n_chol, int mode, size_t budget_bytes, size_t* bytes)
+{
+    cc_ladder_args a{};
+    a.o = o; a.v = v; a.n_chol = n_chol; a.mode = mode; a.budget_bytes = budget_bytes;
+    return cc_ladder_workspace_size_ex(&a, bytes);
+}
+
+int cc_ladder_plan_query(const cc_ladder_args* args, cc_ladder_plan* plan)
+{
+    if (!plan) return CC_ERR_NULL;
+    Ctx c;
+    CC_TRY(make_ctx(args, &c));
+    size_t need = 0;
+    const size_t bytes = args->ws_bytes ? args->ws_bytes : (args->budget_bytes ? args->budget_bytes : kDefaultBudget);
+    const int A = pick_block(c, bytes, args->a_block, &need);
+    if (A < 0) return CC_ERR_WORKSPACE;
+    plan->order = c.order;
+    plan->a_block = A;
+    plan->n_blocks = (c.v + A - 1) / A;
+    plan->slices = c.s;
+    plan->pairs = (int)c.pairs;
+    plan->ws_bytes = need;
+    const double v = c.v, o2 = (double)c.o * c.o;
+    plan->flops_algorithmic = c.order == CC_ORDER_INTEGRAL_FIRST ? 2.0 * (o2 + c.n) * v * v * v * v
+                                                                 : 4.0 * c.n * o2 * v * v * v;
+    const double nprod = c.mode == CC_OZAKI_BF16 ? c.s * (c.s + 1) / 2.0 : 1.0;
+    const double base = c.order == CC_ORDER_INTEGRAL_FIRST ? 2.0 * ((double)c.pairs + c.n) * v * v * v * v
+                                                           : 4.0 * c.n * (double)c.pairs * v * v * v;
+    plan->flops_issued = base * nprod;
+    return CC_OK;
+}
+
+int cc_ladder_fwd_ex(const cc_ladder_args* args) { return fwd_impl(args); }
+
+int cc_ladder_fwd(int o, int v, int n_chol, const double* L, const double* t2, double* R, int mode, double* energy,
+                  void* workspace, size_t ws_bytes, void* stream)
+{
+    cc_ladder_args a{};
+    a.o = o; a.v = v; a.n_chol = n_chol; a.L = L; a.t2 = t2; a.R = R; a.energy = energy; a.mode = mode;
+    a.workspace = workspace; a.ws_bytes = ws_bytes; a.stream = stream;
+    return fwd_impl(&a);
+}
+
+int cc_ladder_bwd_workspace_size(int o, int v, int n_chol, int mode, size_t budget_bytes, size_t* bytes)
+{
+    if (!bytes) return CC_ERR_NULL;
+    BwdPlan bp;
+    CC_TRY(bwd_plan(o, v, n_chol, mode, 0, 0, budget_bytes ? budget_bytes : kDefaultBudget, true, &bp));
+    *bytes = bp.L.total;
+    return CC_OK;
+}
+
+int cc_ladder_bwd_ex(int o, int v, int n_chol, const double* L, const double* t2, const double* dR, double* dL,
+                     double* dt2, int mode, int flags, int slices, void* workspace, size_t ws_bytes, void* stream)
+{
+    return bwd_impl(o, v, n_chol, L, t2, dR, dL, dt2, mode, flags, slices, workspace, ws_bytes, stream);
+}
+
+int cc_ladder_bwd(int o, int v, int n_chol, const double* L, const double* t2, const double* dR, double* dL,
+                  double* dt2, int mode, void* workspace, size_t ws_bytes, void* stream)
+{
+    return bwd_impl(o, v, n_chol, L, t2, dR, dL, dt2, mode, 0, 0, workspace, ws_bytes, stream);
+}
+
+int cc_ladder_energy_workspace_size(int o, int v, size_t* bytes)
+{
+    if (!bytes) return CC_ERR_NULL;
+    if (o < 1 || v < 1) return CC_ERR_SHAPE;
+    *bytes = al256(8 * (size_t)energy_scratch_doubles(o, v)) + al256(8 * (size_t)o * o);
+    return CC_OK;
+}
+
+int cc_ladder_energy(int o, int v, const double* R, const double* t2, double* energy, double* e_pair, void* workspace,
+                     size_t ws_bytes, void* stream)
+{
+    if (o < 1 || v < 1) return CC_ERR_SHAPE;
+    if (!R || !t2 || !energy || !workspace) return CC_ERR_NULL;
+    if (!aligned(R, 16) || !aligned(t2, 16) || !aligned(workspace, 256) || !aligned(energy, 8)) return CC_ERR_ALIGN;
+    size_t need = 0;
+    cc_ladder_energy_workspace_size(o, v, &need);
+    if (ws_bytes < need) return CC_ERR_WORKSPACE;
+    cudaStream_t st = (cudaStream_t)stream;
+    double* part = (double*)workspace;
+    double* ep = e_pair ? e_pair : (double*)((char*)workspace + al256(8 * (size_t)energy_scratch_doubles(o, v)));
+    CC_CU(energy_pairs(o, v, R, t2, part, ep, st));
+    CC_CU(energy_total(o * o, ep, energy, st));
+    CC_CU(cudaGetLastError());
+    return CC_OK;
+}
+
+static size_t gemm_ws(int mode, int M, int N, int K, int s)
+{
+    Carve cv;
+    cv.take(256);
+    if (is_tc(mode)) {
+        const int es = esz_of(mode);
+        cv.take((size_t)es * s * M * pitch_for(K, es));
+        cv.take(4 * (size_t)M);
+        cv.take((size_t)es * s * N * pitch_for(K, es));
+        cv.take(4 * (size_t)N);
+    }
+    return cv.cur;
+}
+
+int cc_ladder_gemm_workspace_size(int mode, int M, int N, int K, int slices, size_t* bytes)
+{
+    if (!bytes) return CC_ERR_NULL;
+    if (M < 1 || N < 1 || K < 1) return CC_ERR_SHAPE;
+    if (mode == CC_OZAKI_INT8) return CC_ERR_UNSUPPORTED;
+    if (mode < CC_FP64 || mode > CC_BF16) return CC_ERR_ARG;
+    if (mode == CC_OZAKI_BF16 && slices != 0 && (slices < 2 || slices > 8)) return CC_ERR_ARG;
+    *bytes = gemm_ws(mode, M, N, K, slices_of(mode, slices));
+    return CC_OK;
+}
+
+int cc_ladder_gemm(int mode, int M, int N, int K, const double* A, int lda, const double* B, int ldb, double* C,
+                   int ldc, int accumulate, int slices, void* workspace, size_t ws_bytes, void* stream)
+{
+    size_t need = 0;
+    CC_TRY(cc_ladder_gemm_workspace_size(mode, M, N, K, slices, &need));
+    if (!A || !B || !C || !workspace) return CC_ERR_NULL;
+    if (lda < K || ldb < K || ldc < N) return CC_ERR_ARG;
+    if (!aligned(A, 16) || !aligned(B, 16) || !aligned(C, 16) || !aligned(workspace, 256)) return CC_ERR_ALIGN;
+    if (ws_bytes < need) return CC_ERR_WORKSPACE;
+    if (is_tc(mode) && !tc_gemm_available()) return CC_ERR_UNSUPPORTED;
+    cudaStream_t st = (cudaStream_t)stream;
+    int* status = (int*)workspace;
+    CC_CU(cudaMemsetAsync(status, 0, 256, st));
+    OutDesc out{C, plain_map(ldc), plain_map(1), accumulate ? 1 : 0};
+    if (mode == CC_FP64) {
+        GemmF64 g{};
+        g.M = M; g.N = N; g.K = K;
+        g.A = A; g.am = plain_map(lda); g.ak = plain_map(1);
+        g.B = B; g.bm = plain_map(ldb); g.bk = plain_map(1);
+        g.out = out;
+        CC_CU(gemm_f64(g, st));
+    } else {
+        Ctx c{};
+        c.mode = mode;
+        c.s = slices_of(mode, slices);
+        const int es = esz_of(mode);
+        Carve cv;
+        cv.take(256);
+        Operand oa{}, ob{};
+        oa.D = at<void>(workspace, cv.take((size_t)es * c.s * M * pitch_for(K, es)));
+        oa.e = at<int>(workspace, cv.take(4 * (size_t)M));
+        ob.D = at<void>(workspace, cv.take((size_t)es * c.s * N * pitch_for(K, es)));
+        ob.e = at<int>(workspace, cv.take(4 * (size_t)N));
+        RowSrc ra{A, plain_map(lda), plain_map(1), M, K};
+        RowSrc rb{B, plain_map(ldb), plain_map(1), N, K};
+        CC_TRY(prep_rows(c, ra, oa, st));
+        CC_TRY(prep_rows(c, rb, ob, st));
+        CC_TRY(run_tc(c, M, N, K, oa, 0, ob, 0, out, status, st));
+    }
+    return finish(status, 0, st);
+}
+
+int cc_ladder_device_status(void* workspace, void* stream)
+{
+    if (!workspace) return CC_ERR_NULL;
+    CC_CU(cudaStreamSynchronize((cudaStream_t)stream));
+    int h[2] = {0, 0};
+    CC_CU(cudaMemcpy(h, workspace, sizeof(h), cudaMemcpyDeviceToHost));
+    CC_CU(cudaMemset(workspace, 0, sizeof(h)));
+    return (h[0] | h[1]) ? CC_ERR_DEVICE_TIMEOUT : CC_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,122 @@
+// cc_internal.cuh -- internal interfaces between the C ABI (api.cu), the planner
+// and the kernels.  Nothing here is part of the public ABI.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/cc_ladder.h"
+
+namespace cc {
+
+// Two-level index map: off(i) = (i / div) * s0 + (i % div) * s1 + base, where the
+// outer term is tab[i / div] instead when a device table is given.  div == 0 means
+// a plain stride: off(i) = i * s1 + base (or tab[i] + base).
+struct Map2 {
+    long long div, s0, s1, base;
+    const long long* tab;
+};
+
+__host__ __device__ inline long long map2(const Map2& m, long long i)
+{
+    if (m.tab) {
+        if (m.div == 0) return m.tab[i] + m.base;
+        return m.tab[i / m.div] + (i % m.div) * m.s1 + m.base;
+    }
+    if (m.div == 0) return i * m.s1 + m.base;
+    return (i / m.div) * m.s0 + (i % m.div) * m.s1 + m.base;
+}
+
+inline Map2 plain_map(long long stride, long long base = 0) { return Map2{0, 0, stride, base, nullptr}; }
+inline Map2 split_map(long long div, long long s0, long long s1, long long base = 0)
+{
+    return Map2{div, s0, s1, base, nullptr};
+}
+inline Map2 table_map(const long long* tab, long long div = 0, long long s1 = 0, long long base = 0)
+{
+    return Map2{div, 0, s1, base, tab};
+}
+
+// Output of every GEMM: C[rmap(m) + cmap(n)] (= or +=) alpha * sum_k A(m,k) B(n,k).
+struct OutDesc {
+    double* C;
+    Map2 rmap, cmap;
+    int accumulate;  // 1: C += ..., 0: C = ...
+};
+
+// ---------------------------------------------------------------- FP64 DMMA GEMM
+// A(m,k) = A[am(m) + ak(k)], B(n,k) = B[bm(n) + bk(k)].  An operand whose k map is
+// the unit stride is loaded k-contiguously, any other one row-contiguously.
+struct GemmF64 {
+    int M, N, K;
+    const double* A; Map2 am, ak;
+    const double* B; Map2 bm, bk;
+    OutDesc out;
+};
+cudaError_t gemm_f64(const GemmF64& g, cudaStream_t s);
+
+// ------------------------------------------------------- tensor-core slice GEMM
+// Operands are K-major "slice stacks": D[slice][row][pitch] of bf16 (or fp32 for
+// TF32), with one int32 exponent per row (row scale 2^e).  For every level L in
+// [level0, level0 + nlevel) the kernel accumulates, in FP32 on the tensor cores,
+// the slice products A_i B_j^T with i + j = L over K-chunks of kchunk[L-level0]
+// elements (one pass per chunk); after each pass the epilogue adds
+// 2^(eA[m] + eB[n] + scale_base - beta*L) * acc into C in FP64.
+enum TcKind { TC_BF16 = 0, TC_TF32 = 1 };
+
+struct GemmTc {
+    int kind;  // TcKind
+    int M, N, K;
+    const void* A; long long pitchA, rowsA, rowA0;  // GEMM row m is stack row rowA0 + m
+    const void* B; long long pitchB, rowsB, rowB0;
+    int slices;                 // slices per operand (1 for the mixed modes)
+    const int* eA; const int* eB;  // per stack-row exponents (nullable = 0)
+    int scale_base, beta;
+    int level0, nlevel;
+    int kchunk[9];              // per level; 0 = whole K; else a multiple of the stage K (64 bf16 / 32 tf32)
+    OutDesc out;
+    int* status;                // device status word (bit 0: wait bound expired)
+    unsigned long long wait_ns; // bound on every device-side wait
+};
+cudaError_t gemm_tc(const GemmTc& g, cudaStream_t s);
+int tc_gemm_available();
+
+// ------------------------------------------------------------------- splitting
+// Row source: X(r, k) = X[rm(r) + km(k)], k contiguous (km.s1 == 1 for the inner level).
+struct RowSrc {
+    const double* X; Map2 rm; Map2 km; long long rows, K;
+};
+// Ozaki split of each row into `s` balanced base-2^beta digits stored as bf16 in
+// D[s][rows][pitch] with exponent e[r] (max |row| < 2^e).  s == 0: plain bf16 copy
+// (e = 0).  D must hold s*rows*pitch bf16.
+cudaError_t split_rows_bf16(const RowSrc& src, int s, int beta, void* D, long long pitch, int* e, cudaStream_t st);
+// Column source, rows contiguous: X(r, k) = X[bmap(r / brows) + r % brows + k * ldk]
+// for r in [0, rows); brows == 0 means one batch (X[r + k * ldk]).
+struct ColSrc {
+    const double* X; long long ldk; long long rows, K;
+    long long brows; Map2 bmap;
+};
+cudaError_t split_cols_bf16(const ColSrc& src, int s, int beta, void* D, long long pitch, int* e,
+                            unsigned long long* scratch_max, cudaStream_t st);
+// Plain fp64 -> tf32 (stored as fp32) copies, K-major.
+cudaError_t convert_rows_tf32(const RowSrc& src, float* D, long long pitch, cudaStream_t st);
+cudaError_t convert_cols_tf32(const ColSrc& src, float* D, long long pitch, cudaStream_t st);
+
+// -------------------------------------------------------------------- misc
+// R[i,j,a,b] (=|+=) Rc[p, a, b] for p = pair(i<=j), and R[j,i,b,a] likewise for i<j.
+cudaError_t scatter_pairs(int o, int v, const double* Rc, double* R, int accumulate, cudaStream_t s);
+// Y[ij][c][d] = X[ij][d][c]
+cudaError_t swap_last2(long long batch, int v, const double* X, double* Y, cudaStream_t s);
+// Y[ij][a][b] = alpha * X[ij][a][b] + X[ji][b][a]   (alpha = 0 or 1)
+cudaError_t add_pair_swap(int o, int v, const double* X, double* Y, int alpha, cudaStream_t s);
+// tab[p] = (i*o + j) * v*v for the pairs i <= j in i-major order
+cudaError_t fill_pair_table(int o, int v, long long* tab, cudaStream_t s);
+// Y[P][a][c] = X[P][c][a]
+cudaError_t transpose_last2(long long batch, int v, const double* X, double* Y, cudaStream_t s);
+// energy
+// part: o*o*ceil(v/32)^2 doubles of scratch; e_pair: o*o results
+cudaError_t energy_pairs(int o, int v, const double* R, const double* t2, double* part, double* e_pair, cudaStream_t s);
+inline long long energy_scratch_doubles(int o, int v) { const long long t = (v + 31) / 32; return (long long)o * o * t * t; }
+cudaError_t energy_total(int npairs, const double* e_pair, double* E, cudaStream_t s);
+
+}  // namespace cc

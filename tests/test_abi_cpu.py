@@ -1,0 +1,115 @@
+"""Host-side checks of the C ABI that need no GPU: the library builds and loads,
+exports every function include/cc_ladder.h declares, and rejects bad arguments
+before it enqueues anything."""
+import ctypes
+import os
+import re
+
+import pytest
+
+from paper_2310_04559_gb300 import _lib, build
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    build.build()
+    return _lib.load()
+
+
+def _declared():
+    txt = open(os.path.join(ROOT, "include", "cc_ladder.h")).read()
+    txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+    return sorted(set(re.findall(r"\b(cc_ladder_\w+)\s*\(", txt)))
+
+
+def test_exports_every_declared_symbol(lib):
+    names = _declared()
+    assert len(names) >= 15
+    for n in names:
+        assert hasattr(lib, n), n
+    assert set(names) == set(_lib.SYMBOLS)
+
+
+def test_version_and_strerror(lib):
+    assert b"sm_103a" in lib.cc_ladder_version()
+    for code in range(-9, 1):
+        assert lib.cc_ladder_strerror(code)
+    assert lib.cc_ladder_strerror(-99) == b"unknown status"
+
+
+def _args(**kw):
+    from paper_2310_04559_gb300.binding import make_args
+    base = dict(o=4, v=24, n=60, mode="fp64")
+    base.update(kw)
+    return make_args(base.pop("o"), base.pop("v"), base.pop("n"), **base)
+
+
+def _fake(addr):
+    return ctypes.c_void_p(addr)
+
+
+def test_argument_errors(lib):
+    a = _args()
+    assert lib.cc_ladder_fwd_ex(ctypes.byref(a)) == -2  # NULL pointers
+    a.L = a.t2 = a.R = _fake(0x10000)
+    a.workspace = _fake(0x20000)
+    a.ws_bytes = 1 << 30
+    a.t2 = _fake(0x10008)  # 8-byte aligned only
+    assert lib.cc_ladder_fwd_ex(ctypes.byref(a)) == -3
+    a.t2 = _fake(0x10000)
+    a.workspace = _fake(0x20080)  # not 256-aligned
+    assert lib.cc_ladder_fwd_ex(ctypes.byref(a)) == -3
+    a.workspace = _fake(0x20000)
+    a.ws_bytes = 1024  # too small for any plan
+    assert lib.cc_ladder_fwd_ex(ctypes.byref(a)) == -4
+    for bad, code in [(dict(o=0), -1), (dict(v=-3), -1), (dict(n=0), -1), (dict(mode="ozaki_int8"), -6)]:
+        b = _args(**bad)
+        b.L = b.t2 = b.R = _fake(0x10000)
+        b.workspace, b.ws_bytes = _fake(0x20000), 1 << 40
+        assert lib.cc_ladder_fwd_ex(ctypes.byref(b)) == code, bad
+    b = _args()
+    b.mode = 17
+    assert lib.cc_ladder_fwd_ex(ctypes.byref(b)) == -9
+    b = _args()
+    b.flags = 1 << 10
+    assert lib.cc_ladder_fwd_ex(ctypes.byref(b)) == -9
+    b = _args(mode="ozaki_bf16", slices=1)
+    assert lib.cc_ladder_fwd_ex(ctypes.byref(b)) == -9
+    # bwd / gemm / energy validation
+    assert lib.cc_ladder_bwd(0, 4, 4, None, None, None, None, None, 0, None, 0, None) == -1
+    assert lib.cc_ladder_bwd(2, 4, 4, None, None, None, None, None, 0, None, 0, None) == -2
+    assert lib.cc_ladder_gemm(0, 4, 4, 0, None, 4, None, 4, None, 4, 0, 0, None, 0, None) == -1
+    assert lib.cc_ladder_gemm(2, 4, 4, 4, None, 4, None, 4, None, 4, 0, 0, None, 0, None) == -6
+    assert lib.cc_ladder_energy(2, 3, None, None, None, None, None, 0, None) == -2
+
+
+def test_workspace_queries_monotone_in_budget(lib):
+    from paper_2310_04559_gb300 import binding as Ld
+    for mode in ["fp64", "ozaki_bf16", "tf32", "bf16"]:
+        for order in ["integral_first", "cholesky_first"]:
+            sizes = []
+            for budget in [1 << 26, 1 << 28, 1 << 30, 1 << 34]:
+                try:
+                    sizes.append(Ld.workspace_size(20, 200, 1000, mode=mode, order=order, budget=budget))
+                except _lib.LadderError as e:
+                    assert e.status == -5
+                    sizes.append(0)
+            assert sizes == sorted(sizes)
+            assert all(s <= b for s, b in zip(sizes, [1 << 26, 1 << 28, 1 << 30, 1 << 34]))
+    # the plan the forward would run for exactly the queried bytes is the same block
+    ws = Ld.workspace_size(40, 400, 2000, mode="ozaki_bf16", symmetric=True, budget=40 << 30)
+    p = Ld.plan(40, 400, 2000, ws_bytes=ws, mode="ozaki_bf16", symmetric=True)
+    assert p["ws_bytes"] == ws and p["n_blocks"] * p["a_block"] >= 400
+    assert p["flops_algorithmic"] == 2.0 * (1600 + 2000) * 400 ** 4
+
+
+def test_planner_orders(lib):
+    from paper_2310_04559_gb300 import binding as Ld
+    # integral-first is cheaper for the o << v << n shapes, Cholesky-first when n o^2 << v
+    assert Ld.plan(40, 400, 2000, mode="ozaki_bf16")["order"] == "integral_first"
+    assert Ld.plan(4, 96, 480, mode="ozaki_bf16")["order"] == "cholesky_first"
+    assert Ld.plan(4, 96, 480, mode="ozaki_bf16", order="integral_first")["order"] == "integral_first"
+    p = Ld.plan(60, 600, 3000, mode="ozaki_bf16", symmetric=True, budget=150 << 30)
+    assert p["ws_bytes"] < 150 << 30 and p["pairs"] == 60 * 61 // 2 and p["slices"] == 6

@@ -1,0 +1,176 @@
+"""GPU parity of the CUDA path (through the C ABI) against the FP64 CPU oracle.
+
+Tolerances (relative Frobenius error ||R - R_oracle|| / ||R_oracle||):
+  fp64        1e-12   DMMA with FP64 accumulation: error ~ sqrt(K) * 2^-53
+  ozaki_bf16  1e-10   6 slices x 7 bits = 42 bits per operand; exact FP32 slice products
+  tf32        1e-2    10-bit mantissa inputs, FP32 accumulation per K-chunk
+  bf16        5e-2    7-bit mantissa inputs
+"""
+import numpy as np
+import pytest
+import torch
+
+from paper_2310_04559_gb300 import binding as B
+from paper_2310_04559_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+TOL = {"fp64": 1e-12, "ozaki_bf16": 1e-10, "tf32": 1e-2, "bf16": 5e-2}
+MODES = list(TOL)
+
+
+@pytest.fixture(scope="module")
+def dev():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    return torch.device("cuda", 0)
+
+
+def rel(a, b):
+    a, b = np.asarray(a), np.asarray(b)
+    return float(np.linalg.norm(a - b) / np.linalg.norm(b))
+
+
+def cu(x, dev):
+    return torch.from_numpy(np.ascontiguousarray(x)).to(dev)
+
+
+# ------------------------------------------------------------- GEMM core
+@pytest.mark.parametrize("mode", MODES)
+@pytest.mark.parametrize("M,N,K", [(1, 1, 1), (37, 300, 70), (200, 513, 1000), (129, 257, 4100)])
+def test_gemm_core(dev, mode, M, N, K):
+    rng = np.random.default_rng(M + N + K)
+    A = rng.standard_normal((M, K)) * np.exp(rng.uniform(-3, 3, (M, 1)))
+    Bm = rng.standard_normal((N, K))
+    ref = A @ Bm.T
+    C = B.gemm(cu(A, dev), cu(Bm, dev), mode=mode).cpu().numpy()
+    assert rel(C, ref) < TOL[mode], (mode, rel(C, ref))
+    # accumulate adds into C
+    C2 = B.gemm(cu(A, dev), cu(Bm, dev), mode=mode, C=cu(ref, dev), accumulate=True).cpu().numpy()
+    assert rel(C2, 2 * ref) < TOL[mode]
+
+
+def test_gemm_ozaki_exact_integers(dev):
+    """Integer inputs that fit in the leading slice give the exact product."""
+    rng = np.random.default_rng(5)
+    A = rng.integers(-40, 41, (130, 300)).astype(np.float64)
+    Bm = rng.integers(-40, 41, (270, 300)).astype(np.float64)
+    C = B.gemm(cu(A, dev), cu(Bm, dev), mode="ozaki_bf16").cpu().numpy()
+    assert np.array_equal(C, A @ Bm.T)
+
+
+# ------------------------------------------------------------ ladder forward
+def _fwd(L, t2, dev, **kw):
+    R = B.ladder_forward(cu(L, dev), cu(t2, dev), **kw)
+    if isinstance(R, tuple):
+        return R[0].cpu().numpy(), float(R[1].cpu())
+    return R.cpu().numpy()
+
+
+@pytest.mark.parametrize("mode", MODES)
+@pytest.mark.parametrize("order", ["integral_first", "cholesky_first"])
+def test_tiny_workload_all_modes(dev, oracle, mode, order):
+    o, v, n = 4, 24, 60
+    L, t2 = synth.ladder_inputs(o, v, n, seed=0)
+    R_ref = oracle.ladder(L, t2)
+    for sym in (False, True):
+        R = _fwd(L, t2, dev, mode=mode, order=order, symmetric=sym)
+        assert rel(R, R_ref) < TOL[mode], (mode, order, sym, rel(R, R_ref))
+
+
+@pytest.mark.parametrize("mode", MODES)
+def test_ragged_multiblock(dev, oracle, mode):
+    """Shapes that span several tiles with ragged tails, non-symmetric L and t2,
+    and forced small a-blocks (ragged last block)."""
+    o, v, n = 5, 37, 150
+    rng = np.random.default_rng(11)
+    L = synth.cholesky_vectors(n, v, symmetric=False, rng=rng)
+    t2 = synth.amplitudes(o, v, symmetric=False, rng=rng)
+    R_ref = oracle.ladder(L, t2)
+    for order in ("integral_first", "cholesky_first"):
+        for ab in (0, 7):
+            R = _fwd(L, t2, dev, mode=mode, order=order, a_block=ab)
+            assert rel(R, R_ref) < TOL[mode], (order, ab, rel(R, R_ref))
+
+
+@pytest.mark.parametrize("mode", ["fp64", "ozaki_bf16"])
+def test_flags_accumulate_exchange_energy(dev, oracle, mode):
+    o, v, n = 3, 29, 41
+    L, t2 = synth.ladder_inputs(o, v, n, seed=3)
+    R_ref = oracle.ladder(L, t2)
+    X_ref = oracle.exchange(L, t2)
+    E_ref = oracle.energy(R_ref, t2)
+    R0 = np.random.default_rng(4).standard_normal(t2.shape)
+    for sym in (False, True):
+        R = B.ladder_forward(cu(L, dev), cu(t2, dev), R=cu(R0, dev), mode=mode, symmetric=sym,
+                             accumulate=True).cpu().numpy()
+        assert rel(R - R0, R_ref) < 10 * TOL[mode]
+        X = _fwd(L, t2, dev, mode=mode, symmetric=sym, exchange=True)
+        assert rel(X, X_ref) < TOL[mode]
+        R, E = _fwd(L, t2, dev, mode=mode, symmetric=sym, energy=True)
+        assert abs(E - E_ref) / abs(E_ref) < TOL[mode]
+    Eg, ep = B.pair_energy(cu(R_ref, dev), cu(t2, dev), pairs=True)
+    E1, ep1 = oracle.energy(R_ref, t2, pair=True)
+    assert abs(float(Eg.cpu()) - E1) <= 1e-13 * abs(E1)
+    assert np.allclose(ep.cpu().numpy(), ep1, rtol=1e-12, atol=1e-15)
+
+
+@pytest.mark.parametrize("mode", ["fp64", "ozaki_bf16"])
+def test_closed_forms_on_device(dev, mode):
+    """L_0 = I (n = 1) gives R = t2; a rank-one L gives an outer product."""
+    o, v = 3, 33
+    t2 = np.random.default_rng(6).standard_normal((o, o, v, v))
+    R = _fwd(np.eye(v)[None], t2, dev, mode=mode)
+    assert rel(R, t2) < TOL[mode]
+    x, y = np.random.default_rng(7).standard_normal((2, v))
+    s = np.einsum("c,ijcd,d->ij", y, t2, y)
+    ref = s[:, :, None, None] * np.outer(x, x)[None, None]
+    R = _fwd(np.outer(x, y)[None], t2, dev, mode=mode)
+    assert rel(R, ref) < TOL[mode]
+
+
+def test_workload_o20_v200_n1000_sampled(dev, oracle):
+    """Full-size o=20, v=200, n=1000 in FP64 and emulated FP64, both orders,
+    checked on sampled `a` columns the oracle computes one by one."""
+    o, v, n = 20, 200, 1000
+    L, t2 = synth.ladder_inputs(o, v, n, seed=0)
+    al = [0, 77, 199]
+    R_ref = oracle.ladder(L, t2, a_list=al)
+    for mode in ("fp64", "ozaki_bf16"):
+        for order in ("integral_first", "cholesky_first"):
+            R = _fwd(L, t2, dev, mode=mode, order=order, symmetric=True, budget=24 << 30)
+            assert rel(R[:, :, al, :], R_ref) < TOL[mode], (mode, order)
+            assert rel(R, R.transpose(1, 0, 3, 2)) < 1e-15 + TOL[mode]
+
+
+# ------------------------------------------------------------------ adjoint
+@pytest.mark.parametrize("mode", ["fp64", "ozaki_bf16"])
+def test_adjoint_vs_oracle(dev, oracle, mode):
+    o, v, n = 3, 14, 23
+    rng = np.random.default_rng(8)
+    L = rng.standard_normal((n, v, v))
+    t2 = rng.standard_normal((o, o, v, v))
+    W = rng.standard_normal((o, o, v, v))
+    dL_ref, dt2_ref = oracle.ladder_grad(L, t2, W)
+    dL, dt2 = B.ladder_backward(cu(L, dev), cu(t2, dev), cu(W, dev), mode=mode)
+    assert rel(dt2.cpu().numpy(), dt2_ref) < TOL[mode]
+    assert rel(dL.cpu().numpy(), dL_ref) < TOL[mode]
+    # pair-symmetric t: one dL pass with W + W^swap
+    ts = synth.amplitudes(o, v, rng=rng)
+    dL_ref, dt2_ref = oracle.ladder_grad(L, ts, W)
+    dL, dt2 = B.ladder_backward(cu(L, dev), cu(ts, dev), cu(W, dev), mode=mode, symmetric=True)
+    assert rel(dt2.cpu().numpy(), dt2_ref) < TOL[mode]
+    assert rel(dL.cpu().numpy(), dL_ref) < TOL[mode]
+
+
+def test_adjoint_autograd_identities(dev):
+    o, v, n = 4, 20, 30
+    L, t2 = synth.ladder_inputs(o, v, n, seed=9)
+    W = synth.cotangent(o, v, seed=10)
+    Lg, tg = cu(L, dev).requires_grad_(), cu(t2, dev).requires_grad_()
+    R = B.ladder(Lg, tg, mode="fp64", symmetric=True)
+    loss = (R * cu(W, dev)).sum()
+    loss.backward()
+    lv = float(loss)
+    assert abs(float((tg.grad * tg).sum()) - lv) < 1e-11 * abs(lv)
+    assert abs(float((Lg.grad * Lg).sum()) - 2 * lv) < 1e-11 * abs(lv)
