@@ -103,6 +103,12 @@ typedef struct cc_ladder_args {
     size_t ws_bytes;       /* its size                                                          */
     size_t budget_bytes;   /* workspace_size_ex only: upper bound for the plan (0 = 150 GB)     */
     void* stream;          /* cudaStream_t                                                      */
+    int a_lo, a_hi;        /* range of virtual indices `a` to compute (both 0 = all of 0..v-1).
+                              Entries written: R[i,j,a,b] for a in [a_lo, a_hi); with
+                              CC_FLAG_SYMMETRIC_T, R[i,j,a,b] (i <= j) and R[j,i,b,a] (i < j) for
+                              a in the range.  Disjoint ranges write disjoint entries, so ranges
+                              spread over devices assemble R by a sum.  energy must be NULL
+                              unless the range is complete.                                      */
 } cc_ladder_args;
 
 /* What the planner decided for a call (for reporting and tests). */
@@ -175,6 +181,22 @@ void cc_ladder_set_wait_limit_ns(unsigned long long ns);
 int cc_ladder_gemm_workspace_size(int mode, int M, int N, int K, int slices, size_t* bytes);
 int cc_ladder_gemm(int mode, int M, int N, int K, const double* A, int lda, const double* B, int ldb, double* C,
                    int ldc, int accumulate, int slices, void* workspace, size_t ws_bytes, void* stream);
+
+/* Tracing.  cc_ladder_profile_enable(1) resets and starts per-phase timing: every phase of
+ * every later call records CUDA events on its stream.  cc_ladder_profile_read synchronises
+ * those events and fills up to max_entries totals (phase name, launches, milliseconds,
+ * tensor-core or FP64 flops issued); it returns the number of phases.  Profiling adds two
+ * events per phase and is off by default.  cc_ladder_launch_count is the number of kernels
+ * the library has launched in this process. */
+typedef struct cc_ladder_profile_entry {
+    char name[32];
+    int launches;
+    double ms;
+    double flops;
+} cc_ladder_profile_entry;
+void cc_ladder_profile_enable(int on);
+int cc_ladder_profile_read(cc_ladder_profile_entry* out, int max_entries);
+long long cc_ladder_launch_count(void);
 
 /* Static description of a status code. */
 const char* cc_ladder_strerror(int status);

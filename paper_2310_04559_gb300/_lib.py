@@ -32,6 +32,7 @@ class Args(ctypes.Structure):
         ("L", _vp), ("t2", _vp), ("R", _vp), ("energy", _vp),
         ("mode", _i), ("order", _i), ("a_block", _i), ("flags", _i), ("slices", _i),
         ("workspace", _vp), ("ws_bytes", _sz), ("budget_bytes", _sz), ("stream", _vp),
+        ("a_lo", _i), ("a_hi", _i),
     ]
 
 
@@ -41,6 +42,11 @@ class Plan(ctypes.Structure):
         ("order", _i), ("a_block", _i), ("n_blocks", _i), ("slices", _i), ("pairs", _i),
         ("ws_bytes", _sz), ("flops_algorithmic", ctypes.c_double), ("flops_issued", ctypes.c_double),
     ]
+
+
+class ProfileEntry(ctypes.Structure):
+    """struct cc_ladder_profile_entry"""
+    _fields_ = [("name", ctypes.c_char * 32), ("launches", _i), ("ms", ctypes.c_double), ("flops", ctypes.c_double)]
 
 
 class LadderError(RuntimeError):
@@ -56,6 +62,7 @@ SYMBOLS = [
     "cc_ladder_fwd_ex", "cc_ladder_bwd_workspace_size", "cc_ladder_bwd", "cc_ladder_bwd_ex", "cc_ladder_energy",
     "cc_ladder_energy_workspace_size", "cc_ladder_device_status", "cc_ladder_set_wait_limit_ns",
     "cc_ladder_strerror", "cc_ladder_version", "cc_ladder_gemm_workspace_size", "cc_ladder_gemm",
+    "cc_ladder_profile_enable", "cc_ladder_profile_read", "cc_ladder_launch_count",
 ]
 
 
@@ -89,11 +96,17 @@ def load(build_if_missing: bool = True):
     L.cc_ladder_set_wait_limit_ns.restype = None
     L.cc_ladder_gemm_workspace_size.argtypes = [_i, _i, _i, _i, _i, ctypes.POINTER(_sz)]
     L.cc_ladder_gemm.argtypes = [_i, _i, _i, _i, _vp, _i, _vp, _i, _vp, _i, _i, _i, _vp, _sz, _vp]
+    L.cc_ladder_profile_enable.argtypes = [_i]
+    L.cc_ladder_profile_enable.restype = None
+    L.cc_ladder_profile_read.argtypes = [ctypes.POINTER(ProfileEntry), _i]
+    L.cc_ladder_launch_count.argtypes = []
+    L.cc_ladder_launch_count.restype = ctypes.c_longlong
     L.cc_ladder_strerror.argtypes = [_i]
     L.cc_ladder_strerror.restype = ctypes.c_char_p
     L.cc_ladder_version.restype = ctypes.c_char_p
     for name in SYMBOLS:
-        if name not in ("cc_ladder_strerror", "cc_ladder_version", "cc_ladder_set_wait_limit_ns"):
+        if name not in ("cc_ladder_strerror", "cc_ladder_version", "cc_ladder_set_wait_limit_ns",
+                        "cc_ladder_profile_enable", "cc_ladder_launch_count"):
             getattr(L, name).restype = _i
     _lib = L
     return L

@@ -67,8 +67,10 @@ def _shapes(L, t2):
 
 
 def make_args(o, v, n, mode="fp64", order="auto", symmetric=False, exchange=False, accumulate=False,
-              a_block=0, slices=0, budget=0, no_sync=False) -> _lib.Args:
+              a_block=0, slices=0, budget=0, no_sync=False, a_range=None) -> _lib.Args:
     a = _lib.Args()
+    if a_range is not None:
+        a.a_lo, a.a_hi = int(a_range[0]), int(a_range[1])
     a.o, a.v, a.n_chol = o, v, n
     a.mode, a.order = _mode(mode), _order(order)
     a.a_block, a.slices = int(a_block), int(slices)
@@ -102,8 +104,10 @@ def alloc_workspace(nbytes: int, device) -> torch.Tensor:
 
 
 def ladder_forward(L, t2, R=None, mode="ozaki_bf16", order="auto", symmetric=False, exchange=False,
-                   accumulate=False, a_block=0, slices=0, energy=False, workspace=None, budget=0, no_sync=False):
-    """R (new tensor unless given) and optionally the pair energy E (0-d tensor)."""
+                   accumulate=False, a_block=0, slices=0, energy=False, workspace=None, budget=0, no_sync=False,
+                   a_range=None):
+    """R (new tensor unless given) and optionally the pair energy E (0-d tensor).
+    a_range=(lo, hi) computes only the columns a in [lo, hi) (see cc_ladder_args)."""
     lib = _lib.load()
     o, v, n = _shapes(L, t2)
     _check_tensor(L, "L", (n, v, v))
@@ -111,7 +115,7 @@ def ladder_forward(L, t2, R=None, mode="ozaki_bf16", order="auto", symmetric=Fal
     if R is None:
         R = torch.empty_like(t2) if not accumulate else torch.zeros_like(t2)
     _check_tensor(R, "R", (o, o, v, v))
-    a = make_args(o, v, n, mode, order, symmetric, exchange, accumulate, a_block, slices, budget, no_sync)
+    a = make_args(o, v, n, mode, order, symmetric, exchange, accumulate, a_block, slices, budget, no_sync, a_range)
     if workspace is None:
         ws = ctypes.c_size_t()
         _lib.check(lib.cc_ladder_workspace_size_ex(ctypes.byref(a), ctypes.byref(ws)), "cc_ladder_workspace_size_ex")
@@ -178,6 +182,24 @@ def gemm(A, B, mode="ozaki_bf16", C=None, accumulate=False, slices=0):
     _lib.check(lib.cc_ladder_gemm(_mode(mode), M, N, K, _ptr(A), K, _ptr(B), K, _ptr(C), N, int(accumulate),
                                   int(slices), _ptr(w), w.numel(), _stream(A.device)), "cc_ladder_gemm")
     return C
+
+
+def profile_enable(on=True):
+    _lib.load().cc_ladder_profile_enable(1 if on else 0)
+
+
+def profile_read() -> dict:
+    """{phase: {"launches", "ms", "flops"}} accumulated since profile_enable(True)."""
+    lib = _lib.load()
+    n = lib.cc_ladder_profile_read(None, 0)
+    arr = (_lib.ProfileEntry * max(n, 1))()
+    n = lib.cc_ladder_profile_read(arr, n)
+    return {arr[i].name.decode(): {"launches": arr[i].launches, "ms": arr[i].ms, "flops": arr[i].flops}
+            for i in range(n)}
+
+
+def launch_count() -> int:
+    return int(_lib.load().cc_ladder_launch_count())
 
 
 class LadderFunction(torch.autograd.Function):

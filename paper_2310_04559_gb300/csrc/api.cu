@@ -31,6 +31,7 @@ namespace {
 constexpr int kDefaultSlices = 6;
 constexpr int kBeta = 7;                 // bits per Ozaki slice (balanced digits in [-64, 64])
 constexpr int kMixedChunk = 16384;       // K elements per FP32 accumulation in the BF16 / TF32 modes
+constexpr int kFixF = 26;                // fixed-point fraction bits (of a level-0 unit) in the Ozaki epilogue
 constexpr size_t kDefaultBudget = 150ull << 30;
 
 std::atomic<unsigned long long> g_wait_ns{2000000000ull};
@@ -162,6 +163,8 @@ int make_ctx(const cc_ladder_args* a, Ctx* c)
     if (a->a_block < 0) return CC_ERR_ARG;
     if (a->flags & ~(CC_FLAG_ACCUMULATE | CC_FLAG_SYMMETRIC_T | CC_FLAG_EXCHANGE | CC_FLAG_NO_STATUS_SYNC)) return CC_ERR_ARG;
     if (a->mode == CC_OZAKI_BF16 && a->slices != 0 && (a->slices < 2 || a->slices > 8)) return CC_ERR_ARG;
+    if (a->a_lo < 0 || a->a_hi < 0 || a->a_lo > a->v || a->a_hi > a->v || (a->a_hi && a->a_hi <= a->a_lo))
+        return CC_ERR_ARG;
     c->o = a->o; c->v = a->v; c->n = a->n_chol;
     c->mode = a->mode; c->flags = a->flags;
     c->s = slices_of(a->mode, a->slices);
@@ -175,6 +178,12 @@ int make_ctx(const cc_ladder_args* a, Ctx* c)
 bool aligned(const void* p, size_t al) { return ((uintptr_t)p % al) == 0; }
 
 int check_cuda(cudaError_t e) { return e == cudaSuccess ? CC_OK : CC_ERR_CUDA; }
+
+int run_f64(const char* name, const GemmF64& g, cudaStream_t st)
+{
+    ProfScope ps(name, st, 2.0 * g.M * (double)g.N * g.K);
+    return check_cuda(gemm_f64(g, st));
+}
 
 #define CC_TRY(x)                      \
     do {                               \
@@ -200,6 +209,7 @@ struct Operand {
 
 int prep_rows(const Ctx& c, const RowSrc& src, Operand& op, cudaStream_t st)
 {
+    ProfScope ps("split", st);
     op.rows = src.rows;
     op.pitch = pitch_for(src.K, esz_of(c.mode));
     if (c.mode == CC_TF32) return check_cuda(convert_rows_tf32(src, (float*)op.D, op.pitch, st));
@@ -209,6 +219,7 @@ int prep_rows(const Ctx& c, const RowSrc& src, Operand& op, cudaStream_t st)
 
 int prep_cols(const Ctx& c, const ColSrc& src, Operand& op, unsigned long long* colmax, cudaStream_t st)
 {
+    ProfScope ps("split", st);
     op.rows = src.rows;
     op.pitch = pitch_for(src.K, esz_of(c.mode));
     if (c.mode == CC_TF32) return check_cuda(convert_cols_tf32(src, (float*)op.D, op.pitch, st));
@@ -216,9 +227,12 @@ int prep_cols(const Ctx& c, const ColSrc& src, Operand& op, unsigned long long* 
     return check_cuda(split_cols_bf16(src, s, kBeta, op.D, op.pitch, op.e, colmax, st));
 }
 
-int run_tc(const Ctx& c, int M, int N, int K, const Operand& A, long long rowA0, const Operand& B, long long rowB0,
-           const OutDesc& out, int* status, cudaStream_t st)
+double tc_products(const Ctx& c) { return c.mode == CC_OZAKI_BF16 ? c.s * (c.s + 1) / 2.0 : 1.0; }
+
+int run_tc(const char* name, const Ctx& c, int M, int N, int K, const Operand& A, long long rowA0, const Operand& B,
+           long long rowB0, const OutDesc& out, int* status, cudaStream_t st)
 {
+    ProfScope ps(name, st, 2.0 * M * (double)N * K * tc_products(c));
     GemmTc g{};
     g.kind = c.mode == CC_TF32 ? TC_TF32 : TC_BF16;
     g.M = M; g.N = N; g.K = K;
@@ -229,9 +243,23 @@ int run_tc(const Ctx& c, int M, int N, int K, const Operand& A, long long rowA0,
     g.eB = c.mode == CC_TF32 ? nullptr : B.e;
     g.beta = kBeta;
     g.scale_base = c.mode == CC_OZAKI_BF16 ? 2 - 2 * kBeta : 0;
-    g.level0 = 0;
-    g.nlevel = c.mode == CC_OZAKI_BF16 ? c.s : 1;
-    for (int i = 0; i < g.nlevel; ++i) g.kchunk[i] = c.mode == CC_OZAKI_BF16 ? 0 : kMixedChunk;
+    if (c.mode == CC_OZAKI_BF16) {
+        // levels 0 .. s-1 (all products i + j <= s-1), paired from the top
+        g.ngroups = 0;
+        for (int L = c.s - 1; L >= 0; L -= 2) {
+            g.glo[g.ngroups] = L >= 1 ? L - 1 : 0;
+            g.gn[g.ngroups] = L >= 1 ? 2 : 1;
+            g.gkc[g.ngroups] = 0;
+            ++g.ngroups;
+        }
+        g.epi = out.accumulate ? EPI_FP64_RMW : EPI_FIXED64;
+        g.fixF = kFixF;
+    } else {
+        g.ngroups = 1;
+        g.glo[0] = 0; g.gn[0] = 1; g.gkc[0] = kMixedChunk;
+        g.epi = EPI_FP64_RMW;
+        g.fixF = 0;
+    }
     g.out = out;
     g.status = status;
     g.wait_ns = g_wait_ns.load();
@@ -260,6 +288,8 @@ int fwd_impl(const cc_ladder_args* a, const double* Lsrc_override = nullptr)
     cudaStream_t st = (cudaStream_t)a->stream;
     const long long o = c.o, v = c.v, n = c.n, vv = v * v;
     int* status = at<int>(ws, Lo.status);
+    const int alo = a->a_hi ? a->a_lo : 0, ahi = a->a_hi ? a->a_hi : c.v;
+    if (a->energy && (alo != 0 || ahi != c.v)) return CC_ERR_UNSUPPORTED;
     CC_CU(cudaMemsetAsync(status, 0, 256, st));
 
     const double* t2 = a->t2;
@@ -287,8 +317,8 @@ int fwd_impl(const cc_ladder_args* a, const double* Lsrc_override = nullptr)
             RowSrc ts{t2, trows, plain_map(1), c.pairs, vv};
             CC_TRY(prep_rows(c, ts, tw, st));
         }
-        for (int a0 = 0; a0 < c.v; a0 += A) {
-            const int Ab = std::min(A, c.v - a0);
+        for (int a0 = alo; a0 < ahi; a0 += A) {
+            const int Ab = std::min(A, ahi - a0);
             // KG1: V[al][b][c][d], GEMM rows (al,c), cols (b,d)
             OutDesc o1{V, split_map(v, v * vv, v), split_map(v, vv, 1), 0};
             if (c.mode == CC_FP64) {
@@ -297,9 +327,9 @@ int fwd_impl(const cc_ladder_args* a, const double* Lsrc_override = nullptr)
                 g.A = Lsrc; g.am = plain_map(1, (long long)a0 * v); g.ak = plain_map(vv);
                 g.B = Lsrc; g.bm = plain_map(1); g.bk = plain_map(vv);
                 g.out = o1;
-                CC_CU(gemm_f64(g, st));
+                CC_TRY(run_f64("kg1_f64", g, st));
             } else {
-                CC_TRY(run_tc(c, Ab * c.v, (int)vv, c.n, Lw, (long long)a0 * v, Lw, 0, o1, status, st));
+                CC_TRY(run_tc("kg1_tc", c, Ab * c.v, (int)vv, c.n, Lw, (long long)a0 * v, Lw, 0, o1, status, st));
             }
             // KG2: R[ij][a0+al][b] = sum_(c,d) t2[ij][(c,d)] V[al][b][(c,d)]
             OutDesc o2{Rdst, plain_map(vv), plain_map(1, (long long)a0 * v), accum};
@@ -309,11 +339,11 @@ int fwd_impl(const cc_ladder_args* a, const double* Lsrc_override = nullptr)
                 g.A = t2; g.am = trows; g.ak = plain_map(1);
                 g.B = V; g.bm = plain_map(vv); g.bk = plain_map(1);
                 g.out = o2;
-                CC_CU(gemm_f64(g, st));
+                CC_TRY(run_f64("kg2_f64", g, st));
             } else {
                 RowSrc vs{V, plain_map(vv), plain_map(1), (long long)Ab * v, vv};
                 CC_TRY(prep_rows(c, vs, Vw, st));
-                CC_TRY(run_tc(c, (int)c.pairs, Ab * c.v, (int)vv, tw, 0, Vw, 0, o2, status, st));
+                CC_TRY(run_tc("kg2_tc", c, (int)c.pairs, Ab * c.v, (int)vv, tw, 0, Vw, 0, o2, status, st));
             }
         }
     } else {
@@ -335,8 +365,8 @@ int fwd_impl(const cc_ladder_args* a, const double* Lsrc_override = nullptr)
             RowSrc lb{Lsrc, plain_map(v), split_map(v, vv, 1), v, n * v};
             CC_TRY(prep_rows(c, lb, LwB, st));
         }
-        for (int a0 = 0; a0 < c.v; a0 += A) {
-            const int Ab = std::min(A, c.v - a0);
+        for (int a0 = alo; a0 < ahi; a0 += A) {
+            const int Ab = std::min(A, ahi - a0);
             // CF1: rows (al, P), cols (p, d), K = c  ->  X2[(p, al), (P, d)]
             OutDesc o1{X2, split_map(n, n * v, v), split_map(v, (long long)Ab * n * v, 1), 0};
             if (c.mode == CC_FP64) {
@@ -345,9 +375,9 @@ int fwd_impl(const cc_ladder_args* a, const double* Lsrc_override = nullptr)
                 g.A = Lsrc; g.am = split_map(n, v, vv, (long long)a0 * v); g.ak = plain_map(1);
                 g.B = t2; g.bm = c.sym ? table_map(pairtab, v, 1) : split_map(v, vv, 1); g.bk = plain_map(v);
                 g.out = o1;
-                CC_CU(gemm_f64(g, st));
+                CC_TRY(run_f64("cf1_f64", g, st));
             } else {
-                CC_TRY(run_tc(c, Ab * c.n, (int)(c.pairs * v), c.v, LwA, (long long)a0 * n, twB, 0, o1, status, st));
+                CC_TRY(run_tc("cf1_tc", c, Ab * c.n, (int)(c.pairs * v), c.v, LwA, (long long)a0 * n, twB, 0, o1, status, st));
             }
             // CF2: rows (p, al), cols b, K = (P, d)  ->  R[p][a0+al][b]
             OutDesc o2{Rdst, split_map(Ab, vv, v, (long long)a0 * v), plain_map(1), accum};
@@ -357,17 +387,21 @@ int fwd_impl(const cc_ladder_args* a, const double* Lsrc_override = nullptr)
                 g.A = X2; g.am = plain_map(n * v); g.ak = plain_map(1);
                 g.B = Lsrc; g.bm = plain_map(v); g.bk = split_map(v, vv, 1);
                 g.out = o2;
-                if (c.sym) g.out.rmap = split_map(Ab, vv, v, (long long)a0 * v);
-                CC_CU(gemm_f64(g, st));
+                CC_TRY(run_f64("cf2_f64", g, st));
             } else {
                 RowSrc xs{X2, plain_map(n * v), plain_map(1), c.pairs * Ab, n * v};
                 CC_TRY(prep_rows(c, xs, X2w, st));
-                CC_TRY(run_tc(c, (int)(c.pairs * Ab), c.v, (int)(n * v), X2w, 0, LwB, 0, o2, status, st));
+                CC_TRY(run_tc("cf2_tc", c, (int)(c.pairs * Ab), c.v, (int)(n * v), X2w, 0, LwB, 0, o2, status, st));
             }
         }
     }
-    if (c.sym) CC_CU(scatter_pairs(c.o, c.v, at<double>(ws, Lo.Rc), a->R, (c.flags & CC_FLAG_ACCUMULATE) ? 1 : 0, st));
+    if (c.sym) {
+        ProfScope ps("scatter", st);
+        CC_CU(scatter_pairs(c.o, c.v, alo, ahi, at<double>(ws, Lo.Rc), a->R, (c.flags & CC_FLAG_ACCUMULATE) ? 1 : 0,
+                            st));
+    }
     if (a->energy) {
+        ProfScope ps("energy", st);
         CC_CU(energy_pairs(c.o, c.v, a->R, a->t2, at<double>(ws, Lo.epart), at<double>(ws, Lo.epair), st));
         CC_CU(energy_total(c.o * c.o, at<double>(ws, Lo.epair), a->energy, st));
     }
@@ -523,11 +557,11 @@ int bwd_impl(int o, int v, int n, const double* L, const double* t2, const doubl
                     g.A = Xs[pass]; g.am = plain_map(1, (long long)e0 * v); g.ak = plain_map(vv);
                     g.B = tt[pass]; g.bm = plain_map(1); g.bk = plain_map(vv);
                     g.out = o1;
-                    CC_CU(gemm_f64(g, st));
+                    CC_TRY(run_f64("m1_f64", g, st));
                 } else {
                     ColSrc ws_{Xs[pass] + (long long)e0 * v, vv, (long long)Eb * v, P, 0, plain_map(0)};
                     CC_TRY(prep_cols(c, ws_, Ww, at<unsigned long long>(ws, Lo.colmax), st));
-                    CC_TRY(run_tc(c, Eb * v, (int)vv, (int)P, Ww, 0, tw, 0, o1, status, st));
+                    CC_TRY(run_tc("m1_tc", c, Eb * v, (int)vv, (int)P, Ww, 0, tw, 0, o1, status, st));
                 }
                 // T1: dL[P][e0+el][f] (+)= sum_(b,d) L[P][(b,d)] M1[(el,f)][(b,d)]
                 OutDesc o2{dL, plain_map(vv), plain_map(1, (long long)e0 * v), pass > 0 ? 1 : 0};
@@ -537,11 +571,11 @@ int bwd_impl(int o, int v, int n, const double* L, const double* t2, const doubl
                     g.A = L; g.am = plain_map(vv); g.ak = plain_map(1);
                     g.B = M1; g.bm = plain_map(vv); g.bk = plain_map(1);
                     g.out = o2;
-                    CC_CU(gemm_f64(g, st));
+                    CC_TRY(run_f64("t1_f64", g, st));
                 } else {
                     RowSrc ms{M1, plain_map(vv), plain_map(1), (long long)Eb * v, vv};
                     CC_TRY(prep_rows(c, ms, M1w, st));
-                    CC_TRY(run_tc(c, n, Eb * v, (int)vv, Lw, 0, M1w, 0, o2, status, st));
+                    CC_TRY(run_tc("t1_tc", c, n, Eb * v, (int)vv, Lw, 0, M1w, 0, o2, status, st));
                 }
             }
         }
@@ -728,7 +762,7 @@ int cc_ladder_gemm(int mode, int M, int N, int K, const double* A, int lda, cons
         g.A = A; g.am = plain_map(lda); g.ak = plain_map(1);
         g.B = B; g.bm = plain_map(ldb); g.bk = plain_map(1);
         g.out = out;
-        CC_CU(gemm_f64(g, st));
+        CC_TRY(run_f64("gemm_f64", g, st));
     } else {
         Ctx c{};
         c.mode = mode;
@@ -745,7 +779,7 @@ int cc_ladder_gemm(int mode, int M, int N, int K, const double* A, int lda, cons
         RowSrc rb{B, plain_map(ldb), plain_map(1), N, K};
         CC_TRY(prep_rows(c, ra, oa, st));
         CC_TRY(prep_rows(c, rb, ob, st));
-        CC_TRY(run_tc(c, M, N, K, oa, 0, ob, 0, out, status, st));
+        CC_TRY(run_tc("gemm_tc", c, M, N, K, oa, 0, ob, 0, out, status, st));
     }
     return finish(status, 0, st);
 }

@@ -57,12 +57,16 @@ cudaError_t gemm_f64(const GemmF64& g, cudaStream_t s);
 
 // ------------------------------------------------------- tensor-core slice GEMM
 // Operands are K-major "slice stacks": D[slice][row][pitch] of bf16 (or fp32 for
-// TF32), with one int32 exponent per row (row scale 2^e).  For every level L in
-// [level0, level0 + nlevel) the kernel accumulates, in FP32 on the tensor cores,
-// the slice products A_i B_j^T with i + j = L over K-chunks of kchunk[L-level0]
-// elements (one pass per chunk); after each pass the epilogue adds
-// 2^(eA[m] + eB[n] + scale_base - beta*L) * acc into C in FP64.
+// TF32), with one int32 exponent per row (row scale 2^e).  The slice-product
+// levels L (products A_i B_j^T with i + j = L) are computed in groups of one or
+// two levels, each group over K-chunks of gkc elements (one pass per chunk), in
+// FP32 on the tensor cores; the epilogue turns level L of a pass into
+// 2^(eA[m] + eB[n] + scale_base - beta*L) * acc, either added into the FP64 output
+// after every pass (EPI_FP64_RMW) or summed exactly as int64 fixed point with
+// 2^-fixF resolution of a level-0 unit and converted once (EPI_FIXED64).
 enum TcKind { TC_BF16 = 0, TC_TF32 = 1 };
+enum TcEpi { EPI_FP64_RMW = 0, EPI_FIXED64 = 1 };
+constexpr int kMaxGroups = 8;
 
 struct GemmTc {
     int kind;  // TcKind
@@ -72,8 +76,11 @@ struct GemmTc {
     int slices;                 // slices per operand (1 for the mixed modes)
     const int* eA; const int* eB;  // per stack-row exponents (nullable = 0)
     int scale_base, beta;
-    int level0, nlevel;
-    int kchunk[9];              // per level; 0 = whole K; else a multiple of the stage K (64 bf16 / 32 tf32)
+    int ngroups;
+    int glo[kMaxGroups];        // lowest level of each group
+    int gn[kMaxGroups];         // levels in the group (1 or 2)
+    int gkc[kMaxGroups];        // K elements per pass (0 = whole K; else a multiple of 64 bf16 / 32 tf32)
+    int epi, fixF;              // TcEpi; fixed-point fraction bits for EPI_FIXED64
     OutDesc out;
     int* status;                // device status word (bit 0: wait bound expired)
     unsigned long long wait_ns; // bound on every device-side wait
@@ -103,8 +110,10 @@ cudaError_t convert_rows_tf32(const RowSrc& src, float* D, long long pitch, cuda
 cudaError_t convert_cols_tf32(const ColSrc& src, float* D, long long pitch, cudaStream_t st);
 
 // -------------------------------------------------------------------- misc
-// R[i,j,a,b] (=|+=) Rc[p, a, b] for p = pair(i<=j), and R[j,i,b,a] likewise for i<j.
-cudaError_t scatter_pairs(int o, int v, const double* Rc, double* R, int accumulate, cudaStream_t s);
+// R[i,j,a,b] (=|+=) Rc[p, a, b] for p = pair(i<=j), and R[j,i,b,a] likewise for i<j,
+// for a in [a_lo, a_hi).
+cudaError_t scatter_pairs(int o, int v, int a_lo, int a_hi, const double* Rc, double* R, int accumulate,
+                          cudaStream_t s);
 // Y[ij][c][d] = X[ij][d][c]
 cudaError_t swap_last2(long long batch, int v, const double* X, double* Y, cudaStream_t s);
 // Y[ij][a][b] = alpha * X[ij][a][b] + X[ji][b][a]   (alpha = 0 or 1)
@@ -118,5 +127,22 @@ cudaError_t transpose_last2(long long batch, int v, const double* X, double* Y, 
 cudaError_t energy_pairs(int o, int v, const double* R, const double* t2, double* part, double* e_pair, cudaStream_t s);
 inline long long energy_scratch_doubles(int o, int v) { const long long t = (v + 31) / 32; return (long long)o * o * t * t; }
 cudaError_t energy_total(int npairs, const double* e_pair, double* E, cudaStream_t s);
+
+// ------------------------------------------------------------------- tracing
+void count_launch(int n = 1);
+// Records CUDA events around a phase on `s` when profiling is enabled.
+class ProfScope {
+  public:
+    ProfScope(const char* name, cudaStream_t s, double flops = 0.0);
+    ~ProfScope();
+    ProfScope(const ProfScope&) = delete;
+    ProfScope& operator=(const ProfScope&) = delete;
+
+  private:
+    const char* name_;
+    cudaStream_t s_;
+    double flops_;
+    void* e0_;
+};
 
 }  // namespace cc

@@ -138,6 +138,7 @@ cudaError_t gemm_f64(const GemmF64& g, cudaStream_t s)
     else if (ak && !bk) gemm_f64_kernel<true, false><<<grid, THREADS, 0, s>>>(g);
     else if (!ak && bk) gemm_f64_kernel<false, true><<<grid, THREADS, 0, s>>>(g);
     else gemm_f64_kernel<false, false><<<grid, THREADS, 0, s>>>(g);
+    count_launch();
     return cudaGetLastError();
 }
 

@@ -1,26 +1,37 @@
 // gemm_tc.cu -- Blackwell (sm_103a) tensor-core GEMM for the emulated-FP64
 // (Ozaki, BF16 slices) and mixed-precision (BF16 / TF32) modes.
 //
-//   C[rmap(m) + cmap(n)] (= or +=) sum_passes 2^(eA[m] + eB[n] + base - beta*level)
-//                                  * sum_{k in pass range} sum_{i+j=level} A_i(m,k) B_j(n,k)
+//   C[rmap(m) + cmap(n)] (= or +=) sum_levels 2^(eA[m] + eB[n] + base - beta*level)
+//                                  * sum_{i+j=level} A_i(m,:) . B_j(n,:)
 //
-// Both operands are K-major slice stacks D[slice][row][pitch].  One CTA owns a
-// 128 x 256 output tile and runs the pass list; within a pass the products
-// A_i B_j^T with i + j = level are accumulated in FP32 in tensor memory (exact
-// for integer-valued slices while partial sums stay below 2^24); at the end of a
-// pass the epilogue adds the scaled FP32 tile into C in FP64.  Two TMEM
-// accumulators (2 x 256 columns) let the MMAs of pass p+1 run while the
-// epilogue drains pass p.
+// Operands are K-major slice stacks D[slice][row][pitch].  One CTA owns a
+// 128 x 256 output tile.  The slice-product levels are processed in groups of
+// at most two (a "pass" = one group over one K-range); each level of a group
+// accumulates in FP32 in its own TMEM accumulator (2 x 256 columns), exact for
+// integer-valued slices while partial sums stay below 2^24.
 //
-// Warp roles (192 threads):
-//   warp 0      TMA producer: 128B-swizzled tiles of A (128 x 128 B) and B
-//               (256 x 128 B) per stage, 4 stages, mbarrier complete_tx.
-//   warp 1      TMEM allocator and MMA issuer: tcgen05.mma.cta_group::1
-//               (M=128, N=256, K=16 bf16 / K=8 tf32) into TMEM, tcgen05.commit
-//               to free a stage / publish an accumulator.
-//   warps 2..5  epilogue: tcgen05.ld (32 lanes x 32 columns), transpose
-//               through shared memory, scaled FP64 read-modify-write of C with
-//               coalesced 256-byte row segments.
+// Operand reuse: for every K-step (64 bf16 / 32 tf32 elements = one 128-byte
+// swizzle atom per row) each slice tile the group needs is loaded once.  The B
+// slices stream in order j = lo..hi through a ring of 32 KB slots; the A slices
+// arrive in order i = hi..lo through a ring of 16 KB slots, so B_j meets every
+// A_i with i + j in the group while A_i lives only until its last partner
+// B_{L2-i} has passed (about two B steps).  For 6 slices the 21 slice products
+// of a K-step cost 24 tile loads instead of 42.
+//
+// Epilogues:
+//   FIXED64  every pass adds its levels, converted exactly to a signed 64-bit
+//            fixed-point number (2^-F of a level-0 unit), into the output tile
+//            held as int64; the last pass scales it once into FP64.  No FP64
+//            arithmetic until that single conversion (GB300's FP64 pipe is slow).
+//   FP64RMW  every pass adds 2^e * acc into the FP64 output (mixed modes, and
+//            accumulation into caller data).  Single-level passes alternate the
+//            two accumulators so the MMAs of pass p+1 overlap the drain of pass p.
+//
+// Warp roles (192 threads): warp 0 TMA producer, warp 1 TMEM allocator + MMA
+// issuer (tcgen05.mma.cta_group::1, M=128, N=256), warps 2..5 epilogue
+// (tcgen05.ld 32 lanes x 32 columns, transpose through shared memory, coalesced
+// global read-modify-write).  CTAs are rastered in groups of M-tiles so the
+// CTAs resident at once share their A and B tiles in L2.
 //
 // Every mbarrier wait is bounded (globaltimer); on expiry the CTA raises a
 // shared abort flag and the device status word, drains the copies and MMAs it
@@ -36,21 +47,22 @@
 namespace cc {
 namespace {
 
-constexpr int BM = 128, BN = 256, STAGES = 4;
-constexpr int ROW_BYTES = 128;                    // K bytes per stage row (one swizzle atom)
-constexpr int A_BYTES = BM * ROW_BYTES;           // 16 KB
-constexpr int B_BYTES = BN * ROW_BYTES;           // 32 KB
-constexpr int STAGE_BYTES = A_BYTES + B_BYTES;    // 48 KB
+constexpr int BM = 128, BN = 256;
+constexpr int ROW_BYTES = 128;                 // K bytes per tile row: one 128-byte swizzle atom
+constexpr int A_TILE = BM * ROW_BYTES;         // 16 KB per A slice tile
+constexpr int B_TILE = BN * ROW_BYTES;         // 32 KB per B slice tile
+constexpr int NA = 4, NB = 4;                  // A ring and B ring slots
+constexpr int TILE_SMEM = NA * A_TILE + NB * B_TILE;  // 192 KB
+constexpr int MAX_SLICES = 8;
 constexpr int EPI_WARPS = 4;
 constexpr int THREADS = 64 + 32 * EPI_WARPS;
 constexpr int TMEM_COLS = 512;
 constexpr unsigned long long kDrainLimitNs = 1000000000ull;  // bound on the abort-path drains
 
 struct SmemCtl {
-    unsigned long long full[STAGES];
-    unsigned long long empty[STAGES];
-    unsigned long long tfull[2];
-    unsigned long long tempty[2];
+    unsigned long long afull[NA], aempty[NA];
+    unsigned long long bfull[NB], bempty[NB];
+    unsigned long long tfull[2], tempty[2];
     unsigned long long drain;
     unsigned int tmem_base;
     volatile int abort;
@@ -59,15 +71,17 @@ struct SmemCtl {
     int eB[BN];
     float stage[EPI_WARPS][32][33];
 };
-constexpr size_t SMEM_BYTES = 1024 + STAGES * STAGE_BYTES + sizeof(SmemCtl);
+constexpr size_t SMEM_BYTES = 1024 + TILE_SMEM + sizeof(SmemCtl);
 
 struct Params {
     int M, N, K;
     long long rowA0, rowB0;
     const int* eA; const int* eB;
     int scale_base, beta, nslices;
-    int nlevel, level0;
-    int kchunk[9];   // per level: K elements per pass (multiple of the stage K), 0 = whole K
+    int ngroups;
+    int glo[kMaxGroups], gn[kMaxGroups], gkc[kMaxGroups];
+    int epi, fixF;
+    int tiles_m, tiles_n, group_m;
     OutDesc out;
     int* status;
     unsigned long long wait_ns;
@@ -154,11 +168,11 @@ __device__ __forceinline__ unsigned long long smem_desc(const void* p)
 {
     const unsigned long long addr = smem_u32(p);
     unsigned long long d = 0;
-    d |= (addr >> 4) & 0x3fffull;              // start address
-    d |= (unsigned long long)1 << 16;          // leading byte offset (unused for swizzled K-major)
-    d |= (unsigned long long)(1024 >> 4) << 32;  // stride byte offset
-    d |= (unsigned long long)1 << 46;          // version
-    d |= (unsigned long long)2 << 61;          // SWIZZLE_128B
+    d |= (addr >> 4) & 0x3fffull;                 // start address
+    d |= (unsigned long long)1 << 16;             // leading byte offset (unused for swizzled K-major)
+    d |= (unsigned long long)(1024 >> 4) << 32;   // stride byte offset: 8 rows x 128 B
+    d |= (unsigned long long)1 << 46;             // version
+    d |= (unsigned long long)2 << 61;             // SWIZZLE_128B
     return d;
 }
 
@@ -219,33 +233,38 @@ __device__ __forceinline__ double pow2(int e)
     return __longlong_as_double((long long)(e + 1023) << 52);
 }
 
-// Pass sequence, shared by all roles: levels level0 .. level0+nlevel-1, each cut
-// into K-chunks.  Returns false past the end.
+// q * 2^sh as a fixed-point integer (round half up for right shifts).
+__device__ __forceinline__ long long fix_shift(int q, int sh)
+{
+    if (sh >= 0) return (long long)q << sh;
+    return ((long long)q + (1ll << (-sh - 1))) >> (-sh);
+}
+
+// Pass sequence shared by all roles: groups in order, each cut into K-chunks.
 struct PassIter {
-    int level, k0, k1;
-    int li;
-    __device__ void begin(const Params& p)
+    int g, k0, k1, idx;
+    __device__ int chunk_end(const Params& p, int from) const
     {
-        li = 0;
-        level = p.level0;
-        k0 = 0;
-        const int kc = p.kchunk[0];
-        k1 = (kc > 0 && kc < p.K) ? kc : p.K;
+        const int kc = p.gkc[g];
+        return (kc > 0 && from + kc < p.K) ? from + kc : p.K;
     }
+    __device__ void begin(const Params& p) { g = 0; k0 = 0; k1 = chunk_end(p, 0); idx = 0; }
     __device__ bool next(const Params& p)
     {
-        if (k1 < p.K) {
-            k0 = k1;
-            const int kc = p.kchunk[li];
-            k1 = (kc > 0 && k0 + kc < p.K) ? k0 + kc : p.K;
-            return true;
-        }
-        if (++li >= p.nlevel) return false;
-        level = p.level0 + li;
+        ++idx;
+        if (k1 < p.K) { k0 = k1; k1 = chunk_end(p, k0); return true; }
+        if (++g >= p.ngroups) return false;
         k0 = 0;
-        const int kc = p.kchunk[li];
-        k1 = (kc > 0 && kc < p.K) ? kc : p.K;
+        k1 = chunk_end(p, 0);
         return true;
+    }
+    __device__ bool last(const Params& p) const { return k1 >= p.K && g == p.ngroups - 1; }
+    // slice index range whose products land in the group's levels
+    __device__ void ranges(const Params& p, int& lo, int& hi) const
+    {
+        const int L1 = p.glo[g], L2 = p.glo[g] + p.gn[g] - 1, s1 = p.nslices - 1;
+        lo = L1 - s1 > 0 ? L1 - s1 : 0;
+        hi = L2 < s1 ? L2 : s1;
     }
 };
 
@@ -255,19 +274,25 @@ gemm_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
 {
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     unsigned char* base = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
-    unsigned char* tiles = base;
-    SmemCtl* ctl = (SmemCtl*)(base + STAGES * STAGE_BYTES);
+    unsigned char* aring = base;                      // NA x A_TILE
+    unsigned char* bring = base + NA * A_TILE;        // NB x B_TILE
+    SmemCtl* ctl = (SmemCtl*)(base + TILE_SMEM);
 
-    constexpr int KSTEP = KIND == TC_BF16 ? 64 : 32;  // K elements per stage
-    constexpr int KMMA = KIND == TC_BF16 ? 16 : 8;    // K per tcgen05.mma
-    constexpr int NMMA = KSTEP / KMMA;                // 4
-
+    constexpr int KSTEP = KIND == TC_BF16 ? 64 : 32;  // K elements per 128-byte row
+    constexpr int NMMA = 4;                           // MMAs (K=16 bf16 / K=8 tf32) per row
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int m0 = blockIdx.y * BM, n0 = blockIdx.x * BN;
 
-    // ---- set-up: barriers, TMEM, per-tile row offsets and exponents
+    // grouped raster: consecutive CTAs walk group_m M-tiles before the next N-tile
+    const int per_group = p.group_m * p.tiles_n;
+    const int t = blockIdx.x;
+    const int first_m = (t / per_group) * p.group_m;
+    const int gm = min(p.tiles_m - first_m, p.group_m);
+    const int m0 = (first_m + (t % per_group) % gm) * BM;
+    const int n0 = ((t % per_group) / gm) * BN;
+
     if (threadIdx.x == 0) {
-        for (int s = 0; s < STAGES; ++s) { mbar_init(&ctl->full[s], 1); mbar_init(&ctl->empty[s], 1); }
+        for (int s = 0; s < NA; ++s) { mbar_init(&ctl->afull[s], 1); mbar_init(&ctl->aempty[s], 1); }
+        for (int s = 0; s < NB; ++s) { mbar_init(&ctl->bfull[s], 1); mbar_init(&ctl->bempty[s], 1); }
         for (int b = 0; b < 2; ++b) { mbar_init(&ctl->tfull[b], 1); mbar_init(&ctl->tempty[b], EPI_WARPS); }
         mbar_init(&ctl->drain, 1);
         ctl->abort = 0;
@@ -294,36 +319,57 @@ gemm_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
 
     if (warp == 0) {
         // ------------------------------------------------------------ producer
+        // Per K-step: for j = lo..hi, first the A tiles (in order i = hi..lo) down to
+        // the lowest i that B_j needs, then B_j.
         if (lane == 0) {
             asm volatile("prefetch.tensormap [%0];" ::"l"((unsigned long long)&tmA) : "memory");
             asm volatile("prefetch.tensormap [%0];" ::"l"((unsigned long long)&tmB) : "memory");
-            int stage = 0;
-            uint32_t phase = 0;
-            long long issued = 0;
+            long long a_issued = 0, b_issued = 0;
             bool ok = true;
             PassIter it;
             it.begin(p);
             do {
-                const int lo = it.level - (p.nslices - 1) > 0 ? it.level - (p.nslices - 1) : 0;
-                const int hi = it.level < p.nslices - 1 ? it.level : p.nslices - 1;
+                int lo, hi;
+                it.ranges(p, lo, hi);
+                const int L1 = p.glo[it.g];
                 for (int kb = it.k0; kb < it.k1 && ok; kb += KSTEP) {
-                    for (int i = lo; i <= hi && ok; ++i) {
-                        if (!mbar_wait(&ctl->empty[stage], phase ^ 1, ctl, p.status, p.wait_ns)) { ok = false; break; }
-                        unsigned char* sa = tiles + stage * STAGE_BYTES;
-                        mbar_expect_tx(&ctl->full[stage], STAGE_BYTES);
-                        tma_load_3d(sa, &tmA, &ctl->full[stage], kb, (int)(p.rowA0 + m0), i);
-                        tma_load_3d(sa + A_BYTES, &tmB, &ctl->full[stage], kb, (int)(p.rowB0 + n0), it.level - i);
-                        ++issued;
-                        if (++stage == STAGES) { stage = 0; phase ^= 1; }
+                    int a_here = 0;
+                    for (int j = lo; j <= hi && ok; ++j) {
+                        const int imin = L1 - j > lo ? L1 - j : lo;
+                        while (a_here < hi - imin + 1) {
+                            const int as = (int)(a_issued % NA);
+                            if (!mbar_wait(&ctl->aempty[as], (uint32_t)(((a_issued / NA) & 1) ^ 1), ctl, p.status,
+                                           p.wait_ns)) {
+                                ok = false;
+                                break;
+                            }
+                            mbar_expect_tx(&ctl->afull[as], A_TILE);
+                            tma_load_3d(aring + as * A_TILE, &tmA, &ctl->afull[as], kb, (int)(p.rowA0 + m0), hi - a_here);
+                            ++a_issued;
+                            ++a_here;
+                        }
+                        if (!ok) break;
+                        const int bs = (int)(b_issued % NB);
+                        if (!mbar_wait(&ctl->bempty[bs], (uint32_t)(((b_issued / NB) & 1) ^ 1), ctl, p.status,
+                                       p.wait_ns)) {
+                            ok = false;
+                            break;
+                        }
+                        mbar_expect_tx(&ctl->bfull[bs], B_TILE);
+                        tma_load_3d(bring + bs * B_TILE, &tmB, &ctl->bfull[bs], kb, (int)(p.rowB0 + n0), j);
+                        ++b_issued;
                     }
                 }
             } while (ok && it.next(p));
             if (!ok) {
-                // drain: the last min(issued, STAGES) stages may still have copies in flight
-                const long long n = issued < STAGES ? issued : STAGES;
-                for (long long q = 1; q <= n; ++q) {
-                    const long long u = issued - q;  // use index of that copy
-                    mbar_drain_wait(&ctl->full[u % STAGES], (uint32_t)((u / STAGES) & 1), p.status);
+                // drain: the newest copy into each A slot and each B slot may still be in flight
+                for (long long q = 1; q <= (a_issued < NA ? a_issued : NA); ++q) {
+                    const long long u = a_issued - q;
+                    mbar_drain_wait(&ctl->afull[u % NA], (uint32_t)((u / NA) & 1), p.status);
+                }
+                for (long long q = 1; q <= (b_issued < NB ? b_issued : NB); ++q) {
+                    const long long u = b_issued - q;
+                    mbar_drain_wait(&ctl->bfull[u % NB], (uint32_t)((u / NB) & 1), p.status);
                 }
             }
         }
@@ -331,42 +377,76 @@ gemm_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
         // ----------------------------------------------------------------- MMA
         if (lane == 0) {
             const uint32_t idesc = instr_desc<KIND>();
-            int stage = 0;
-            uint32_t phase = 0;
-            int pass = 0;
+            long long a_used = 0, b_used = 0;
+            unsigned tuse[2] = {0, 0};
+            int toggle = 0;
             bool ok = true, any = false;
             PassIter it;
             it.begin(p);
             do {
-                const int buf = pass & 1;
-                const uint32_t use = (uint32_t)(pass >> 1);
-                if (!mbar_wait(&ctl->tempty[buf], (use & 1) ^ 1, ctl, p.status, p.wait_ns)) { ok = false; break; }
+                int lo, hi;
+                it.ranges(p, lo, hi);
+                const int L1 = p.glo[it.g], nl = p.gn[it.g], L2 = L1 + nl - 1;
+                int bufs[2], nb;
+                if (nl == 2) { bufs[0] = 0; bufs[1] = 1; nb = 2; }
+                else { bufs[0] = toggle; bufs[1] = toggle; toggle ^= 1; nb = 1; }
+                for (int q = 0; q < nb && ok; ++q)
+                    if (!mbar_wait(&ctl->tempty[bufs[q]], (tuse[bufs[q]] & 1) ^ 1, ctl, p.status, p.wait_ns)) ok = false;
+                if (!ok) break;
                 fence_after();
-                const uint32_t d = tmem + (uint32_t)(buf * BN);
-                const int lo = it.level - (p.nslices - 1) > 0 ? it.level - (p.nslices - 1) : 0;
-                const int hi = it.level < p.nslices - 1 ? it.level : p.nslices - 1;
-                uint32_t acc = 0;
+                uint32_t acc_on[2] = {0, 0};
                 for (int kb = it.k0; kb < it.k1 && ok; kb += KSTEP) {
-                    for (int i = lo; i <= hi; ++i) {
-                        if (!mbar_wait(&ctl->full[stage], phase, ctl, p.status, p.wait_ns)) { ok = false; break; }
-                        fence_after();
-                        unsigned char* sa = tiles + stage * STAGE_BYTES;
-                        const unsigned long long ad = smem_desc(sa), bd = smem_desc(sa + A_BYTES);
-#pragma unroll
-                        for (int j = 0; j < NMMA; ++j) {
-                            // advance the start address by 32 bytes per MMA K-step
-                            mma<KIND>(d, ad + (unsigned long long)((j * 32) >> 4), bd + (unsigned long long)((j * 32) >> 4),
-                                      idesc, acc);
-                            acc = 1;
+                    int a_wait = 0, a_free = 0;  // A tiles of this K-step waited for / released (i = hi - index)
+                    for (int j = lo; j <= hi; ++j) {
+                        const int imin = L1 - j > lo ? L1 - j : lo;
+                        const int imax = L2 - j < hi ? L2 - j : hi;
+                        while (a_wait < hi - imin + 1) {
+                            const long long u = a_used + a_wait;
+                            if (!mbar_wait(&ctl->afull[u % NA], (uint32_t)((u / NA) & 1), ctl, p.status, p.wait_ns)) {
+                                ok = false;
+                                break;
+                            }
+                            ++a_wait;
                         }
-                        any = true;
-                        mma_commit(&ctl->empty[stage]);
-                        if (++stage == STAGES) { stage = 0; phase ^= 1; }
+                        if (!ok) break;
+                        const int bs = (int)(b_used % NB);
+                        if (!mbar_wait(&ctl->bfull[bs], (uint32_t)((b_used / NB) & 1), ctl, p.status, p.wait_ns)) {
+                            ok = false;
+                            break;
+                        }
+                        fence_after();
+                        const unsigned long long bdesc = smem_desc(bring + bs * B_TILE);
+                        for (int i = imax; i >= imin; --i) {
+                            const int lv = i + j - L1;
+                            const uint32_t d = tmem + (uint32_t)(bufs[lv] * BN);
+                            const int as = (int)((a_used + (hi - i)) % NA);
+                            const unsigned long long ad = smem_desc(aring + as * A_TILE);
+#pragma unroll
+                            for (int k = 0; k < NMMA; ++k) {
+                                // advance the start address by 32 bytes per MMA K-step
+                                mma<KIND>(d, ad + (unsigned long long)(2 * k), bdesc + (unsigned long long)(2 * k), idesc,
+                                          k == 0 ? acc_on[lv] : 1u);
+                            }
+                            acc_on[lv] = 1;
+                            any = true;
+                        }
+                        mma_commit(&ctl->bempty[bs]);
+                        ++b_used;
+                        // release the A tiles no later B of this K-step needs: i > min(hi, L2 - j - 1)
+                        const int keep = j < hi ? (L2 - j - 1 < hi ? L2 - j - 1 : hi) : lo - 1;
+                        while (a_free < hi - keep) {
+                            mma_commit(&ctl->aempty[(a_used + a_free) % NA]);
+                            ++a_free;
+                        }
                     }
+                    if (!ok) break;
+                    a_used += hi - lo + 1;
                 }
                 if (!ok) break;
-                mma_commit(&ctl->tfull[buf]);
-                ++pass;
+                for (int q = 0; q < nb; ++q) {
+                    mma_commit(&ctl->tfull[bufs[q]]);
+                    ++tuse[bufs[q]];
+                }
             } while (it.next(p));
             if (!ok && any) {
                 mma_commit(&ctl->drain);
@@ -375,42 +455,78 @@ gemm_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
         }
     } else {
         // ------------------------------------------------------------ epilogue
-        const int q = warp & 3;  // TMEM lane quarter this warp may access
-        const int row0 = q * 32;
+        const int q4 = warp & 3;  // TMEM lane quarter this warp may access
+        const int row0 = q4 * 32;
         float(*stg)[33] = ctl->stage[warp - 2];
-        int pass = 0;
+        unsigned tuse[2] = {0, 0};
+        int toggle = 0;
         PassIter it;
         it.begin(p);
+        bool ok = true;
         do {
-            const int buf = pass & 1;
-            const uint32_t use = (uint32_t)(pass >> 1);
-            if (!mbar_wait(&ctl->tfull[buf], use & 1, ctl, p.status, p.wait_ns)) break;
+            const int L1 = p.glo[it.g], nl = p.gn[it.g];
+            int bufs[2], nb;
+            if (nl == 2) { bufs[0] = 0; bufs[1] = 1; nb = 2; }
+            else { bufs[0] = toggle; bufs[1] = toggle; toggle ^= 1; nb = 1; }
+            for (int q = 0; q < nb && ok; ++q)
+                if (!mbar_wait(&ctl->tfull[bufs[q]], tuse[bufs[q]] & 1, ctl, p.status, p.wait_ns)) ok = false;
+            if (!ok) break;
             fence_after();
-            const bool store_only = (pass == 0) && !p.out.accumulate;
-            const int lvl_shift = p.scale_base - p.beta * it.level;
+            const bool first = it.idx == 0, last = it.last(p);
             for (int c = 0; c < BN / 32; ++c) {
-                float v[32];
-                tmem_ld32(tmem + ((uint32_t)row0 << 16) + (uint32_t)(buf * BN + c * 32), v);
-#pragma unroll
-                for (int j = 0; j < 32; ++j) stg[lane][j] = v[j];
-                __syncwarp();
                 const int n = n0 + c * 32 + lane;
                 const bool ncol = n < p.N;
                 const long long co = ncol ? map2(p.out.cmap, n) : 0;
-                const int eb = ctl->eB[c * 32 + lane] + lvl_shift;
-                for (int r = 0; r < 32; ++r) {
-                    const long long ro = ctl->rowoff[row0 + r];
-                    if (ro < 0 || !ncol) continue;
-                    const double x = (double)stg[r][lane] * pow2(ctl->eA[row0 + r] + eb);
-                    double* dst = p.out.C + ro + co;
-                    *dst = store_only ? x : *dst + x;
+                if (p.epi == EPI_FIXED64) {
+                    long long X[32];
+#pragma unroll
+                    for (int r = 0; r < 32; ++r) X[r] = 0;
+                    for (int q = 0; q < nb; ++q) {
+                        float v[32];
+                        tmem_ld32(tmem + ((uint32_t)row0 << 16) + (uint32_t)(bufs[q] * BN + c * 32), v);
+#pragma unroll
+                        for (int j = 0; j < 32; ++j) stg[lane][j] = v[j];
+                        __syncwarp();
+                        const int sh = p.fixF - p.beta * (L1 + q);
+#pragma unroll
+                        for (int r = 0; r < 32; ++r) X[r] += fix_shift(__float2int_rn(stg[r][lane]), sh);
+                        __syncwarp();
+                    }
+                    const int eb = ctl->eB[c * 32 + lane] + p.scale_base - p.fixF;
+#pragma unroll
+                    for (int r = 0; r < 32; ++r) {
+                        const long long ro = ctl->rowoff[row0 + r];
+                        if (ro < 0 || !ncol) continue;
+                        long long* dst = (long long*)(p.out.C + ro + co);
+                        const long long tot = first ? X[r] : *dst + X[r];
+                        if (last) *(double*)dst = (double)tot * pow2(ctl->eA[row0 + r] + eb);
+                        else *dst = tot;
+                    }
+                } else {
+                    for (int q = 0; q < nb; ++q) {
+                        float v[32];
+                        tmem_ld32(tmem + ((uint32_t)row0 << 16) + (uint32_t)(bufs[q] * BN + c * 32), v);
+#pragma unroll
+                        for (int j = 0; j < 32; ++j) stg[lane][j] = v[j];
+                        __syncwarp();
+                        const bool store_only = first && q == 0 && !p.out.accumulate;
+                        const int eb = ctl->eB[c * 32 + lane] + p.scale_base - p.beta * (L1 + q);
+                        for (int r = 0; r < 32; ++r) {
+                            const long long ro = ctl->rowoff[row0 + r];
+                            if (ro < 0 || !ncol) continue;
+                            const double x = (double)stg[r][lane] * pow2(ctl->eA[row0 + r] + eb);
+                            double* dst = p.out.C + ro + co;
+                            *dst = store_only ? x : *dst + x;
+                        }
+                        __syncwarp();
+                    }
                 }
-                __syncwarp();
             }
             fence_before();
             __syncwarp();
-            if (lane == 0) mbar_arrive(&ctl->tempty[buf]);
-            ++pass;
+            if (lane == 0)
+                for (int q = 0; q < nb; ++q) mbar_arrive(&ctl->tempty[bufs[q]]);
+            for (int q = 0; q < nb; ++q) ++tuse[bufs[q]];
         } while (it.next(p));
     }
 
@@ -436,7 +552,8 @@ PFN_cuTensorMapEncodeTiled_v12000 get_encode()
     return fn;
 }
 
-// 3-D map over a slice stack [slices][rows][pitch] with extent K in the inner dim.
+// 3-D map over a slice stack [slices][rows][pitch] with extent K in the inner dim;
+// box = one 128-byte swizzle atom of K by box_rows rows.
 bool make_map(CUtensorMap* m, const void* base, int kind, long long K, long long pitch, long long rows, int slices,
               int box_rows)
 {
@@ -460,42 +577,50 @@ int tc_gemm_available() { return get_encode() != nullptr; }
 cudaError_t gemm_tc(const GemmTc& g, cudaStream_t s)
 {
     if (g.M <= 0 || g.N <= 0) return cudaSuccess;
-    if (g.K <= 0 || g.slices < 1 || g.slices > 8 || g.nlevel < 1 || g.nlevel > 9) return cudaErrorInvalidValue;
-    if (g.level0 < 0 || g.level0 + g.nlevel - 1 > 2 * (g.slices - 1)) return cudaErrorInvalidValue;
+    if (g.K <= 0 || g.slices < 1 || g.slices > MAX_SLICES || g.ngroups < 1 || g.ngroups > kMaxGroups)
+        return cudaErrorInvalidValue;
     const int kstep = g.kind == TC_BF16 ? 64 : 32;
     Params p{};
     p.M = g.M; p.N = g.N; p.K = g.K;
     p.rowA0 = g.rowA0; p.rowB0 = g.rowB0;
     p.eA = g.eA; p.eB = g.eB;
     p.scale_base = g.scale_base; p.beta = g.beta; p.nslices = g.slices;
-    p.nlevel = g.nlevel;
-    p.level0 = g.level0;
-    for (int i = 0; i < g.nlevel; ++i) {
-        if (g.kchunk[i] < 0 || g.kchunk[i] % kstep) return cudaErrorInvalidValue;
-        p.kchunk[i] = g.kchunk[i];
+    p.ngroups = g.ngroups;
+    for (int i = 0; i < g.ngroups; ++i) {
+        if (g.gn[i] < 1 || g.gn[i] > 2 || g.glo[i] < 0 || g.glo[i] + g.gn[i] - 1 > 2 * (g.slices - 1))
+            return cudaErrorInvalidValue;
+        if (g.gkc[i] < 0 || g.gkc[i] % kstep) return cudaErrorInvalidValue;
+        p.glo[i] = g.glo[i]; p.gn[i] = g.gn[i]; p.gkc[i] = g.gkc[i];
     }
+    if (g.epi == EPI_FIXED64 && g.out.accumulate) return cudaErrorInvalidValue;
+    p.epi = g.epi;
+    p.fixF = g.fixF;
     p.out = g.out;
     p.status = g.status;
     p.wait_ns = g.wait_ns;
+    p.tiles_m = (g.M + BM - 1) / BM;
+    p.tiles_n = (g.N + BN - 1) / BN;
+    p.group_m = p.tiles_m < 16 ? p.tiles_m : 16;
     CUtensorMap ma, mb;
     if (!make_map(&ma, g.A, g.kind, g.K, g.pitchA, g.rowsA, g.slices, BM)) return cudaErrorInvalidValue;
     if (!make_map(&mb, g.B, g.kind, g.K, g.pitchB, g.rowsB, g.slices, BN)) return cudaErrorInvalidValue;
-    dim3 grid((g.N + BN - 1) / BN, (g.M + BM - 1) / BM);
-    if (grid.y > 65535) return cudaErrorInvalidConfiguration;
+    const long long ntiles = (long long)p.tiles_m * p.tiles_n;
+    if (ntiles > 0x7fffffffll) return cudaErrorInvalidConfiguration;
     static bool attr_done[2] = {false, false};
     if (g.kind == TC_BF16) {
         if (!attr_done[0]) {
             cudaFuncSetAttribute(gemm_tc_kernel<TC_BF16>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SMEM_BYTES);
             attr_done[0] = true;
         }
-        gemm_tc_kernel<TC_BF16><<<grid, THREADS, SMEM_BYTES, s>>>(ma, mb, p);
+        gemm_tc_kernel<TC_BF16><<<(unsigned)ntiles, THREADS, SMEM_BYTES, s>>>(ma, mb, p);
     } else {
         if (!attr_done[1]) {
             cudaFuncSetAttribute(gemm_tc_kernel<TC_TF32>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SMEM_BYTES);
             attr_done[1] = true;
         }
-        gemm_tc_kernel<TC_TF32><<<grid, THREADS, SMEM_BYTES, s>>>(ma, mb, p);
+        gemm_tc_kernel<TC_TF32><<<(unsigned)ntiles, THREADS, SMEM_BYTES, s>>>(ma, mb, p);
     }
+    count_launch();
     return cudaGetLastError();
 }
 

@@ -94,13 +94,14 @@ __global__ void transpose_kernel(long long batch, int v, const double* __restric
     }
 }
 
-// R[i,j,a,b] (=|+=) Rc[p,a,b]; for i < j also R[j,i,b,a] (=|+=) Rc[p,a,b].
-__global__ void scatter_pairs_kernel(int o, int v, const double* __restrict__ Rc, double* __restrict__ R,
-                                     int accumulate)
+// R[i,j,a,b] (=|+=) Rc[p,a,b]; for i < j also R[j,i,b,a] (=|+=) Rc[p,a,b]; a in [a_lo, a_hi).
+__global__ void scatter_pairs_kernel(int o, int v, int a_lo, int a_hi, const double* __restrict__ Rc,
+                                     double* __restrict__ R, int accumulate)
 {
     __shared__ double S[T][T + 1];
     const int ntile = (v + T - 1) / T;
     const int ta = blockIdx.x / ntile, tb = blockIdx.x % ntile;
+    const int a0 = a_lo + ta * T;
     const int p = blockIdx.y;
     int i, j;
     pair_of(o, p, i, j);
@@ -109,8 +110,8 @@ __global__ void scatter_pairs_kernel(int o, int v, const double* __restrict__ Rc
     double* Rij = R + ((long long)i * o + j) * vv;
     double* Rji = R + ((long long)j * o + i) * vv;
     for (int y = threadIdx.y; y < T; y += TR) {
-        const int a = ta * T + y, b = tb * T + threadIdx.x;
-        if (a < v && b < v) {
+        const int a = a0 + y, b = tb * T + threadIdx.x;
+        if (a < a_hi && b < v) {
             const long long q = (long long)a * v + b;
             const double x = Rp[q];
             S[y][threadIdx.x] = x;
@@ -120,8 +121,8 @@ __global__ void scatter_pairs_kernel(int o, int v, const double* __restrict__ Rc
     if (i == j) return;
     __syncthreads();
     for (int y = threadIdx.y; y < T; y += TR) {
-        const int b = tb * T + y, a = ta * T + threadIdx.x;
-        if (a < v && b < v) {
+        const int b = tb * T + y, a = a0 + threadIdx.x;
+        if (a < a_hi && b < v) {
             const long long q = (long long)b * v + a;
             const double x = S[threadIdx.x][y];
             Rji[q] = accumulate ? Rji[q] + x : x;
@@ -180,20 +181,25 @@ cudaError_t energy_pairs(int o, int v, const double* R, const double* t2, double
     const int ntile = (v + T - 1) / T;
     energy_tiles_kernel<<<dim3(ntile * ntile, o * o), dim3(T, TR), 0, s>>>(v, R, t2, part);
     row_sum_kernel<<<o * o, 256, 0, s>>>((long long)ntile * ntile, part, e_pair);
+    count_launch(2);
     return cudaGetLastError();
 }
 
 cudaError_t energy_total(int npairs, const double* e_pair, double* E, cudaStream_t s)
 {
     row_sum_kernel<<<1, 256, 0, s>>>(npairs, e_pair, E);
+    count_launch();
     return cudaGetLastError();
 }
 
-cudaError_t scatter_pairs(int o, int v, const double* Rc, double* R, int accumulate, cudaStream_t s)
+cudaError_t scatter_pairs(int o, int v, int a_lo, int a_hi, const double* Rc, double* R, int accumulate,
+                          cudaStream_t s)
 {
     const int ntile = (v + T - 1) / T;
+    const int ntile_a = (a_hi - a_lo + T - 1) / T;
     const int np = o * (o + 1) / 2;
-    scatter_pairs_kernel<<<dim3(ntile * ntile, np), dim3(T, TR), 0, s>>>(o, v, Rc, R, accumulate);
+    scatter_pairs_kernel<<<dim3(ntile_a * ntile, np), dim3(T, TR), 0, s>>>(o, v, a_lo, a_hi, Rc, R, accumulate);
+    count_launch();
     return cudaGetLastError();
 }
 
@@ -201,6 +207,7 @@ cudaError_t swap_last2(long long batch, int v, const double* X, double* Y, cudaS
 {
     const int ntile = (v + T - 1) / T;
     transpose_kernel<<<batch_grid(ntile * ntile, batch), dim3(T, TR), 0, s>>>(batch, v, X, Y);
+    count_launch();
     return cudaGetLastError();
 }
 
@@ -213,6 +220,7 @@ cudaError_t add_pair_swap(int o, int v, const double* X, double* Y, int alpha, c
 {
     const int ntile = (v + T - 1) / T;
     add_pair_swap_kernel<<<dim3(ntile * ntile, o * o), dim3(T, TR), 0, s>>>(o, v, X, Y, alpha);
+    count_launch();
     return cudaGetLastError();
 }
 
@@ -220,6 +228,7 @@ cudaError_t fill_pair_table(int o, int v, long long* tab, cudaStream_t s)
 {
     const int np = o * (o + 1) / 2;
     fill_pair_table_kernel<<<(np + 127) / 128, 128, 0, s>>>(o, (long long)v * v, tab);
+    count_launch();
     return cudaGetLastError();
 }
 

@@ -212,6 +212,7 @@ cudaError_t split_rows_bf16(const RowSrc& src, int s, int beta, void* D, long lo
     } else {
         split_rows_kernel<32><<<(unsigned)((src.rows + 7) / 8), 256, 0, st>>>(src, s, beta, (__nv_bfloat16*)D, pitch, e);
     }
+    count_launch();
     return cudaGetLastError();
 }
 
@@ -226,9 +227,11 @@ cudaError_t split_cols_bf16(const ColSrc& src, int s, int beta, void* D, long lo
         const long long kchunk = 256;
         dim3 g((unsigned)((src.rows + 255) / 256), (unsigned)((src.K + kchunk - 1) / kchunk));
         col_max_kernel<<<g, 256, 0, st>>>(src, kchunk, scratch_max);
+        count_launch();
     }
     dim3 g2((unsigned)((src.rows + CT_R - 1) / CT_R), (unsigned)((src.K + CT_K - 1) / CT_K));
     split_cols_kernel<<<g2, dim3(32, 8), 0, st>>>(src, s, beta, scratch_max, (__nv_bfloat16*)D, pitch, e);
+    count_launch();
     return cudaGetLastError();
 }
 
@@ -236,6 +239,7 @@ cudaError_t convert_rows_tf32(const RowSrc& src, float* D, long long pitch, cuda
 {
     if (src.rows <= 0) return cudaSuccess;
     convert_rows_tf32_kernel<<<(unsigned)src.rows, 256, 0, st>>>(src, D, pitch);
+    count_launch();
     return cudaGetLastError();
 }
 
@@ -244,6 +248,7 @@ cudaError_t convert_cols_tf32(const ColSrc& src, float* D, long long pitch, cuda
     if (src.rows <= 0) return cudaSuccess;
     dim3 g2((unsigned)((src.rows + CT_R - 1) / CT_R), (unsigned)((src.K + CT_K - 1) / CT_K));
     convert_cols_tf32_kernel<<<g2, dim3(32, 8), 0, st>>>(src, D, pitch);
+    count_launch();
     return cudaGetLastError();
 }
 
