@@ -493,14 +493,21 @@ gemm_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
                         __syncwarp();
                     }
                     const int eb = ctl->eB[c * 32 + lane] + p.scale_base - p.fixF;
+                    // all loads of the chunk are issued before any store (no aliasing stalls)
+                    if (!first) {
+#pragma unroll
+                        for (int r = 0; r < 32; ++r) {
+                            const long long ro = ctl->rowoff[row0 + r];
+                            if (ro >= 0 && ncol) X[r] += __ldcg((const long long*)(p.out.C + ro + co));
+                        }
+                    }
 #pragma unroll
                     for (int r = 0; r < 32; ++r) {
                         const long long ro = ctl->rowoff[row0 + r];
                         if (ro < 0 || !ncol) continue;
                         long long* dst = (long long*)(p.out.C + ro + co);
-                        const long long tot = first ? X[r] : *dst + X[r];
-                        if (last) *(double*)dst = (double)tot * pow2(ctl->eA[row0 + r] + eb);
-                        else *dst = tot;
+                        if (last) __stcg((double*)dst, (double)X[r] * pow2(ctl->eA[row0 + r] + eb));
+                        else __stcg(dst, X[r]);
                     }
                 } else {
                     for (int q = 0; q < nb; ++q) {
@@ -511,12 +518,17 @@ gemm_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
                         __syncwarp();
                         const bool store_only = first && q == 0 && !p.out.accumulate;
                         const int eb = ctl->eB[c * 32 + lane] + p.scale_base - p.beta * (L1 + q);
+                        double old[32];
+#pragma unroll
+                        for (int r = 0; r < 32; ++r) {
+                            const long long ro = ctl->rowoff[row0 + r];
+                            old[r] = (!store_only && ro >= 0 && ncol) ? __ldcg(p.out.C + ro + co) : 0.0;
+                        }
+#pragma unroll
                         for (int r = 0; r < 32; ++r) {
                             const long long ro = ctl->rowoff[row0 + r];
                             if (ro < 0 || !ncol) continue;
-                            const double x = (double)stg[r][lane] * pow2(ctl->eA[row0 + r] + eb);
-                            double* dst = p.out.C + ro + co;
-                            *dst = store_only ? x : *dst + x;
+                            __stcg(p.out.C + ro + co, old[r] + (double)stg[r][lane] * pow2(ctl->eA[row0 + r] + eb));
                         }
                         __syncwarp();
                     }
