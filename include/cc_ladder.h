@@ -55,7 +55,8 @@ enum cc_status {
     CC_ERR_UNSUPPORTED = -6,    /* mode / order / flag combination not available    */
     CC_ERR_CUDA = -7,           /* a CUDA runtime call failed                       */
     CC_ERR_DEVICE_TIMEOUT = -8, /* a bounded device-side wait ran out; results invalid */
-    CC_ERR_ARG = -9             /* other invalid argument (unknown mode, bad a_block) */
+    CC_ERR_ARG = -9,            /* other invalid argument (unknown mode, bad a_block) */
+    CC_ERR_NOALLOC_LIMIT = -10  /* problem larger than cc_ladder_energy_noalloc's fixed scratch */
 };
 
 /* Arithmetic used for the two contractions (integral build and ladder GEMM). */
@@ -164,6 +165,22 @@ int cc_ladder_bwd_ex(int o, int v, int n_chol, const double* L, const double* t2
 int cc_ladder_energy(int o, int v, const double* R, const double* t2, double* energy, double* e_pair,
                      void* workspace, size_t ws_bytes, void* stream);
 int cc_ladder_energy_workspace_size(int o, int v, size_t* bytes);
+
+/* Pair energy without any allocation and without a workspace (the paper has no counterpart:
+ * this entry point exists for callers that cannot allocate device memory -- e.g. code whose device
+ * memory belongs to another framework's pool, or code that must not call cudaMalloc/cudaFree
+ * because those calls can block or synchronise the device).  Same result and kernels as
+ * cc_ladder_energy; the partial sums live in a 16 MiB array inside the library that every GPU
+ * loading the library holds until the process exits.
+ *   Limit: ceil(v/32)^2 * o^2 doubles of partials, plus o^2 when e_pair is NULL, must not exceed
+ *   2^21 (e.g. o = 60 with v <= 640); larger problems return CC_ERR_NOALLOC_LIMIT and launch nothing.
+ *   The first call on each device looks up the array's device address (cudaGetSymbolAddress, with
+ *   that device current); make that first call before capturing the stream into a graph.
+ *   All calls share the one array: calls whose kernels may overlap on the GPU (different streams,
+ *   or different host threads on one device) race and must be serialised by the caller.
+ *   Nothing is synchronised; errors of the kernels surface at the caller's next synchronisation. */
+int cc_ladder_energy_noalloc(int o, int v, const double* R, const double* t2, double* energy, double* e_pair,
+                             void* stream);
 
 /* Device status word of a workspace after calls made with CC_FLAG_NO_STATUS_SYNC
  * (synchronises `stream`; returns CC_OK or CC_ERR_DEVICE_TIMEOUT and clears the word). */

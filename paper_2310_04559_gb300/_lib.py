@@ -15,6 +15,7 @@ CC_OK = 0
 STATUS = {
     0: "CC_OK", -1: "CC_ERR_SHAPE", -2: "CC_ERR_NULL", -3: "CC_ERR_ALIGN", -4: "CC_ERR_WORKSPACE",
     -5: "CC_ERR_BUDGET", -6: "CC_ERR_UNSUPPORTED", -7: "CC_ERR_CUDA", -8: "CC_ERR_DEVICE_TIMEOUT", -9: "CC_ERR_ARG",
+    -10: "CC_ERR_NOALLOC_LIMIT",
 }
 MODES = {"fp64": 0, "ozaki_bf16": 1, "ozaki_int8": 2, "tf32": 3, "bf16": 4}
 ORDERS = {"auto": 0, "integral_first": 1, "cholesky_first": 2}
@@ -62,7 +63,7 @@ SYMBOLS = [
     "cc_ladder_fwd_ex", "cc_ladder_bwd_workspace_size", "cc_ladder_bwd", "cc_ladder_bwd_ex", "cc_ladder_energy",
     "cc_ladder_energy_workspace_size", "cc_ladder_device_status", "cc_ladder_set_wait_limit_ns",
     "cc_ladder_strerror", "cc_ladder_version", "cc_ladder_gemm_workspace_size", "cc_ladder_gemm",
-    "cc_ladder_profile_enable", "cc_ladder_profile_read", "cc_ladder_launch_count",
+    "cc_ladder_profile_enable", "cc_ladder_profile_read", "cc_ladder_launch_count", "cc_ladder_energy_noalloc",
 ]
 
 
@@ -101,6 +102,7 @@ def load(build_if_missing: bool = True):
     L.cc_ladder_profile_read.argtypes = [ctypes.POINTER(ProfileEntry), _i]
     L.cc_ladder_launch_count.argtypes = []
     L.cc_ladder_launch_count.restype = ctypes.c_longlong
+    L.cc_ladder_energy_noalloc.argtypes = [_i, _i, _vp, _vp, _vp, _vp, _vp]
     L.cc_ladder_strerror.argtypes = [_i]
     L.cc_ladder_strerror.restype = ctypes.c_char_p
     L.cc_ladder_version.restype = ctypes.c_char_p

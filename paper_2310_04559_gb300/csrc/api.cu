@@ -606,6 +606,7 @@ const char* cc_ladder_strerror(int status)
     case CC_ERR_CUDA: return "CUDA runtime error";
     case CC_ERR_DEVICE_TIMEOUT: return "a bounded device-side wait expired; results are invalid";
     case CC_ERR_ARG: return "invalid argument";
+    case CC_ERR_NOALLOC_LIMIT: return "problem exceeds the fixed scratch of cc_ladder_energy_noalloc";
     default: return "unknown status";
     }
 }

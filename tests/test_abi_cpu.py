@@ -34,7 +34,7 @@ def test_exports_every_declared_symbol(lib):
 
 def test_version_and_strerror(lib):
     assert b"sm_103a" in lib.cc_ladder_version()
-    for code in range(-9, 1):
+    for code in range(-10, 1):
         assert lib.cc_ladder_strerror(code)
     assert lib.cc_ladder_strerror(-99) == b"unknown status"
 
