@@ -217,6 +217,17 @@ int prep_rows(const Ctx& c, const RowSrc& src, Operand& op, cudaStream_t st)
     return check_cuda(split_rows_bf16(src, s, kBeta, op.D, op.pitch, op.e, st));
 }
 
+// Split of an intermediate left as int64 fixed point by run_tc(..., intermediate=true).
+int prep_fixed(const Ctx& c, const FixedSrc& src, Operand& op, cudaStream_t st)
+{
+    ProfScope ps("split", st);
+    op.rows = src.rows;
+    op.pitch = pitch_for((long long)src.outer * src.inner, esz_of(c.mode));
+    return check_cuda(split_fixed_rows_bf16(src, c.s, kBeta, op.D, op.pitch, op.e, st));
+}
+
+constexpr int kFixedBase = 2 - 2 * kBeta - kFixF;  // exponent of one fixed-point unit, before row/col exponents
+
 int prep_cols(const Ctx& c, const ColSrc& src, Operand& op, unsigned long long* colmax, cudaStream_t st)
 {
     ProfScope ps("split", st);
@@ -229,8 +240,10 @@ int prep_cols(const Ctx& c, const ColSrc& src, Operand& op, unsigned long long* 
 
 double tc_products(const Ctx& c) { return c.mode == CC_OZAKI_BF16 ? c.s * (c.s + 1) / 2.0 : 1.0; }
 
+// intermediate: the output feeds another slice GEMM through split_fixed_rows, so in
+// the emulated mode it stays int64 fixed point (no FP64 work, no loads in the epilogue).
 int run_tc(const char* name, const Ctx& c, int M, int N, int K, const Operand& A, long long rowA0, const Operand& B,
-           long long rowB0, const OutDesc& out, int* status, cudaStream_t st)
+           long long rowB0, const OutDesc& out, int* status, cudaStream_t st, bool intermediate = false)
 {
     ProfScope ps(name, st, 2.0 * M * (double)N * K * tc_products(c));
     GemmTc g{};
@@ -252,7 +265,7 @@ int run_tc(const char* name, const Ctx& c, int M, int N, int K, const Operand& A
             g.gkc[g.ngroups] = 0;
             ++g.ngroups;
         }
-        g.epi = out.accumulate ? EPI_FP64_RMW : EPI_FIXED64;
+        g.epi = out.accumulate ? EPI_FP64_RMW : (intermediate ? EPI_FIXED64_RED : EPI_FIXED64);
         g.fixF = kFixF;
     } else {
         g.ngroups = 1;
@@ -329,7 +342,7 @@ int fwd_impl(const cc_ladder_args* a, const double* Lsrc_override = nullptr)
                 g.out = o1;
                 CC_TRY(run_f64("kg1_f64", g, st));
             } else {
-                CC_TRY(run_tc("kg1_tc", c, Ab * c.v, (int)vv, c.n, Lw, (long long)a0 * v, Lw, 0, o1, status, st));
+                CC_TRY(run_tc("kg1_tc", c, Ab * c.v, (int)vv, c.n, Lw, (long long)a0 * v, Lw, 0, o1, status, st, true));
             }
             // KG2: R[ij][a0+al][b] = sum_(c,d) t2[ij][(c,d)] V[al][b][(c,d)]
             OutDesc o2{Rdst, plain_map(vv), plain_map(1, (long long)a0 * v), accum};
@@ -341,8 +354,15 @@ int fwd_impl(const cc_ladder_args* a, const double* Lsrc_override = nullptr)
                 g.out = o2;
                 CC_TRY(run_f64("kg2_f64", g, st));
             } else {
-                RowSrc vs{V, plain_map(vv), plain_map(1), (long long)Ab * v, vv};
-                CC_TRY(prep_rows(c, vs, Vw, st));
+                if (c.mode == CC_OZAKI_BF16) {
+                    // V[al][b][c][d] = X * 2^(eL[(a0+al)v + c] + eL[b v + d] + base)
+                    FixedSrc fs{(const long long*)V, (long long)Ab * v, vv, c.v, c.v, Lw.e,
+                                split_map(v, v, 0, (long long)a0 * v), Lw.e, split_map(v, 0, v), kFixedBase};
+                    CC_TRY(prep_fixed(c, fs, Vw, st));
+                } else {
+                    RowSrc vs{V, plain_map(vv), plain_map(1), (long long)Ab * v, vv};
+                    CC_TRY(prep_rows(c, vs, Vw, st));
+                }
                 CC_TRY(run_tc("kg2_tc", c, (int)c.pairs, Ab * c.v, (int)vv, tw, 0, Vw, 0, o2, status, st));
             }
         }
@@ -377,7 +397,8 @@ int fwd_impl(const cc_ladder_args* a, const double* Lsrc_override = nullptr)
                 g.out = o1;
                 CC_TRY(run_f64("cf1_f64", g, st));
             } else {
-                CC_TRY(run_tc("cf1_tc", c, Ab * c.n, (int)(c.pairs * v), c.v, LwA, (long long)a0 * n, twB, 0, o1, status, st));
+                CC_TRY(run_tc("cf1_tc", c, Ab * c.n, (int)(c.pairs * v), c.v, LwA, (long long)a0 * n, twB, 0, o1, status, st,
+                              true));
             }
             // CF2: rows (p, al), cols b, K = (P, d)  ->  R[p][a0+al][b]
             OutDesc o2{Rdst, split_map(Ab, vv, v, (long long)a0 * v), plain_map(1), accum};
@@ -389,8 +410,15 @@ int fwd_impl(const cc_ladder_args* a, const double* Lsrc_override = nullptr)
                 g.out = o2;
                 CC_TRY(run_f64("cf2_f64", g, st));
             } else {
-                RowSrc xs{X2, plain_map(n * v), plain_map(1), c.pairs * Ab, n * v};
-                CC_TRY(prep_rows(c, xs, X2w, st));
+                if (c.mode == CC_OZAKI_BF16) {
+                    // X2[(p, al)][(P, d)] = X * 2^(eLA[(a0+al) n + P] + etB[p v + d] + base)
+                    FixedSrc fs{(const long long*)X2, c.pairs * Ab, n * v, c.n, c.v, LwA.e,
+                                split_map(Ab, 0, n, (long long)a0 * n), twB.e, split_map(Ab, v, 0), kFixedBase};
+                    CC_TRY(prep_fixed(c, fs, X2w, st));
+                } else {
+                    RowSrc xs{X2, plain_map(n * v), plain_map(1), c.pairs * Ab, n * v};
+                    CC_TRY(prep_rows(c, xs, X2w, st));
+                }
                 CC_TRY(run_tc("cf2_tc", c, (int)(c.pairs * Ab), c.v, (int)(n * v), X2w, 0, LwB, 0, o2, status, st));
             }
         }
@@ -561,7 +589,7 @@ int bwd_impl(int o, int v, int n, const double* L, const double* t2, const doubl
                 } else {
                     ColSrc ws_{Xs[pass] + (long long)e0 * v, vv, (long long)Eb * v, P, 0, plain_map(0)};
                     CC_TRY(prep_cols(c, ws_, Ww, at<unsigned long long>(ws, Lo.colmax), st));
-                    CC_TRY(run_tc("m1_tc", c, Eb * v, (int)vv, (int)P, Ww, 0, tw, 0, o1, status, st));
+                    CC_TRY(run_tc("m1_tc", c, Eb * v, (int)vv, (int)P, Ww, 0, tw, 0, o1, status, st, true));
                 }
                 // T1: dL[P][e0+el][f] (+)= sum_(b,d) L[P][(b,d)] M1[(el,f)][(b,d)]
                 OutDesc o2{dL, plain_map(vv), plain_map(1, (long long)e0 * v), pass > 0 ? 1 : 0};
@@ -573,8 +601,15 @@ int bwd_impl(int o, int v, int n, const double* L, const double* t2, const doubl
                     g.out = o2;
                     CC_TRY(run_f64("t1_f64", g, st));
                 } else {
-                    RowSrc ms{M1, plain_map(vv), plain_map(1), (long long)Eb * v, vv};
-                    CC_TRY(prep_rows(c, ms, M1w, st));
+                    if (mode == CC_OZAKI_BF16) {
+                        // M1[el][f][b][d] = X * 2^(eW[el v + b] + et[f v + d] + base)
+                        FixedSrc fs{(const long long*)M1, (long long)Eb * v, vv, v, v, Ww.e, split_map(v, v, 0), tw.e,
+                                    split_map(v, 0, v), kFixedBase};
+                        CC_TRY(prep_fixed(c, fs, M1w, st));
+                    } else {
+                        RowSrc ms{M1, plain_map(vv), plain_map(1), (long long)Eb * v, vv};
+                        CC_TRY(prep_rows(c, ms, M1w, st));
+                    }
                     CC_TRY(run_tc("t1_tc", c, n, Eb * v, (int)vv, Lw, 0, M1w, 0, o2, status, st));
                 }
             }

@@ -65,7 +65,7 @@ cudaError_t gemm_f64(const GemmF64& g, cudaStream_t s);
 // after every pass (EPI_FP64_RMW) or summed exactly as int64 fixed point with
 // 2^-fixF resolution of a level-0 unit and converted once (EPI_FIXED64).
 enum TcKind { TC_BF16 = 0, TC_TF32 = 1 };
-enum TcEpi { EPI_FP64_RMW = 0, EPI_FIXED64 = 1 };
+enum TcEpi { EPI_FP64_RMW = 0, EPI_FIXED64 = 1, EPI_FIXED64_RED = 2 };
 constexpr int kMaxGroups = 8;
 
 struct GemmTc {
@@ -105,6 +105,18 @@ struct ColSrc {
 };
 cudaError_t split_cols_bf16(const ColSrc& src, int s, int beta, void* D, long long pitch, int* e,
                             unsigned long long* scratch_max, cudaStream_t st);
+// Ozaki split of an int64 fixed-point intermediate (a slice-GEMM output kept as
+// EPI_FIXED64_RED).  Row r, element k = o*inner + i is X[r*ldx + k] * 2^e with
+// e = eA[amap(r) + o] + eB[bmap(r) + i] + base.  Integer arithmetic only.
+struct FixedSrc {
+    const long long* X; long long rows, ldx;
+    int outer, inner;
+    const int* eA; Map2 amap;
+    const int* eB; Map2 bmap;
+    int base;
+};
+cudaError_t split_fixed_rows_bf16(const FixedSrc& src, int s, int beta, void* D, long long pitch, int* e,
+                                  cudaStream_t st);
 // Plain fp64 -> tf32 (stored as fp32) copies, K-major.
 cudaError_t convert_rows_tf32(const RowSrc& src, float* D, long long pitch, cudaStream_t st);
 cudaError_t convert_cols_tf32(const ColSrc& src, float* D, long long pitch, cudaStream_t st);

@@ -23,6 +23,9 @@
 //            fixed-point number (2^-F of a level-0 unit), into the output tile
 //            held as int64; the last pass scales it once into FP64.  No FP64
 //            arithmetic until that single conversion (GB300's FP64 pipe is slow).
+//   FIXED64_RED  as FIXED64 but the output stays int64 fixed point: the first pass
+//            stores, later passes add with red.global (no loads in the epilogue); the
+//            split kernel that consumes the intermediate applies the exponents.
 //   FP64RMW  every pass adds 2^e * acc into the FP64 output (mixed modes, and
 //            accumulation into caller data).  Single-level passes alternate the
 //            two accumulators so the MMAs of pass p+1 overlap the drain of pass p.
@@ -477,7 +480,7 @@ gemm_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
                 const int n = n0 + c * 32 + lane;
                 const bool ncol = n < p.N;
                 const long long co = ncol ? map2(p.out.cmap, n) : 0;
-                if (p.epi == EPI_FIXED64) {
+                if (p.epi != EPI_FP64_RMW) {
                     long long X[32];
 #pragma unroll
                     for (int r = 0; r < 32; ++r) X[r] = 0;
@@ -493,6 +496,18 @@ gemm_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
                         __syncwarp();
                     }
                     const int eb = ctl->eB[c * 32 + lane] + p.scale_base - p.fixF;
+                    if (p.epi == EPI_FIXED64_RED) {
+                        // int64 result for a consumer that scales it: store, then add without reading
+#pragma unroll
+                        for (int r = 0; r < 32; ++r) {
+                            const long long ro = ctl->rowoff[row0 + r];
+                            if (ro < 0 || !ncol) continue;
+                            unsigned long long* dst = (unsigned long long*)(p.out.C + ro + co);
+                            if (first) __stcg((long long*)dst, X[r]);
+                            else atomicAdd(dst, (unsigned long long)X[r]);
+                        }
+                        continue;
+                    }
                     // all loads of the chunk are issued before any store (no aliasing stalls)
                     if (!first) {
 #pragma unroll
@@ -604,7 +619,7 @@ cudaError_t gemm_tc(const GemmTc& g, cudaStream_t s)
         if (g.gkc[i] < 0 || g.gkc[i] % kstep) return cudaErrorInvalidValue;
         p.glo[i] = g.glo[i]; p.gn[i] = g.gn[i]; p.gkc[i] = g.gkc[i];
     }
-    if (g.epi == EPI_FIXED64 && g.out.accumulate) return cudaErrorInvalidValue;
+    if (g.epi != EPI_FP64_RMW && g.out.accumulate) return cudaErrorInvalidValue;
     p.epi = g.epi;
     p.fixF = g.fixF;
     p.out = g.out;

@@ -21,6 +21,8 @@
 // through a shared-memory transpose.
 #include <cuda_bf16.h>
 
+#include <climits>
+
 #include "cc_internal.cuh"
 
 namespace cc {
@@ -169,6 +171,68 @@ __global__ void split_cols_kernel(const ColSrc src, int s, int beta, const unsig
     }
 }
 
+// X * 2^sh rounded to an integer (round half up for right shifts); |result| < 2^62.
+__device__ __forceinline__ long long shift_round(long long X, int sh)
+{
+    if (sh >= 0) return X << sh;
+    if (sh <= -63) return 0;
+    return (X + (1ll << (-sh - 1))) >> (-sh);
+}
+
+// One CTA (8 warps) per row; warp w walks outer indices w, w+8, ..., lanes the inner index.
+__global__ void split_fixed_kernel(const FixedSrc src, int s, int beta, __nv_bfloat16* __restrict__ D, long long pitch,
+                                   int* __restrict__ e_out)
+{
+    extern __shared__ int esm[];  // outer entries of eA, then inner entries of eB
+    __shared__ int red[8];
+    const long long r = blockIdx.x;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const long long ab = map2(src.amap, r), bb = map2(src.bmap, r);
+    for (int q = threadIdx.x; q < src.outer; q += 256) esm[q] = src.eA[ab + q];
+    for (int q = threadIdx.x; q < src.inner; q += 256) esm[src.outer + q] = src.eB[bb + q];
+    __syncthreads();
+    const int* eo = esm;
+    const int* ei = esm + src.outer;
+    const long long* Xr = src.X + r * src.ldx;
+    // pass 1: E = max over the row of bitlength(|X|) + e, so that max |value| < 2^E
+    int mx = INT_MIN;
+    for (int o = warp; o < src.outer; o += 8) {
+        const long long* Xo = Xr + (long long)o * src.inner;
+        for (int i = lane; i < src.inner; i += 32) {
+            const long long x = __ldcs(Xo + i);
+            if (x) {
+                const unsigned long long ax = x < 0 ? (unsigned long long)(-x) : (unsigned long long)x;
+                const int c = 64 - __clzll((long long)ax) + eo[o] + ei[i];
+                mx = c > mx ? c : mx;
+            }
+        }
+    }
+    for (int w = 16; w > 0; w >>= 1) mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, w));
+    if (lane == 0) red[warp] = mx;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int m = red[0];
+        for (int w = 1; w < 8; ++w) m = max(m, red[w]);
+        red[0] = m;
+    }
+    __syncthreads();
+    const bool zero = red[0] == INT_MIN;
+    const int E = zero ? 0 : red[0] + src.base;
+    if (threadIdx.x == 0) e_out[r] = E;
+    // pass 2: digits of round(value * 2^(beta*s - 1 - E))
+    const int total = beta * s;
+    const long long slice_stride = src.rows * pitch;
+    __nv_bfloat16* Dr = D + r * pitch;
+    for (int o = warp; o < src.outer; o += 8) {
+        const long long* Xo = Xr + (long long)o * src.inner;
+        for (int i = lane; i < src.inner; i += 32) {
+            const long long x = zero ? 0 : __ldcs(Xo + i);
+            const long long X = shift_round(x, eo[o] + ei[i] + src.base + total - 1 - E);
+            digits_bf16(X, s, beta, Dr + (long long)o * src.inner + i, slice_stride);
+        }
+    }
+}
+
 __device__ __forceinline__ float to_tf32(double x)
 {
     const float f = (float)x;
@@ -231,6 +295,18 @@ cudaError_t split_cols_bf16(const ColSrc& src, int s, int beta, void* D, long lo
     }
     dim3 g2((unsigned)((src.rows + CT_R - 1) / CT_R), (unsigned)((src.K + CT_K - 1) / CT_K));
     split_cols_kernel<<<g2, dim3(32, 8), 0, st>>>(src, s, beta, scratch_max, (__nv_bfloat16*)D, pitch, e);
+    count_launch();
+    return cudaGetLastError();
+}
+
+cudaError_t split_fixed_rows_bf16(const FixedSrc& src, int s, int beta, void* D, long long pitch, int* e,
+                                  cudaStream_t st)
+{
+    if (src.rows <= 0) return cudaSuccess;
+    if (s < 1 || s > 8 || beta < 2 || beta > 9 || beta * s > 62) return cudaErrorInvalidValue;
+    const size_t smem = sizeof(int) * ((size_t)src.outer + src.inner);
+    if (smem > 48 * 1024) return cudaErrorInvalidValue;
+    split_fixed_kernel<<<(unsigned)src.rows, 256, smem, st>>>(src, s, beta, (__nv_bfloat16*)D, pitch, e);
     count_launch();
     return cudaGetLastError();
 }
