@@ -54,7 +54,8 @@ constexpr int BM = 128, BN = 256;
 constexpr int ROW_BYTES = 128;                 // K bytes per tile row: one 128-byte swizzle atom
 constexpr int A_TILE = BM * ROW_BYTES;         // 16 KB per A slice tile
 constexpr int B_TILE = BN * ROW_BYTES;         // 32 KB per B slice tile
-constexpr int NA = 4, NB = 4;                  // A ring and B ring slots
+constexpr int NA = 4, NB = 4;                  // A ring and B ring slots (powers of two)
+static_assert((NA & (NA - 1)) == 0 && (NB & (NB - 1)) == 0, "ring sizes must be powers of two");
 constexpr int TILE_SMEM = NA * A_TILE + NB * B_TILE;  // 192 KB
 constexpr int MAX_SLICES = 8;
 constexpr int EPI_WARPS = 4;
@@ -165,6 +166,30 @@ __device__ __forceinline__ void tma_load_3d(void* dst, const CUtensorMap* map, u
         : "memory");
 }
 
+// Multicast load: the box lands at the same shared-memory offset in every CTA of
+// `mask` and completes `bar` (same offset) in each of them.
+__device__ __forceinline__ void tma_load_3d_mc(void* dst, const CUtensorMap* map, unsigned long long* bar, int x, int y,
+                                               int z, uint16_t mask)
+{
+    asm volatile(
+        "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes.multicast::cluster"
+        " [%0], [%1, {%2, %3, %4}], [%5], %6;"
+        ::"r"(smem_u32(dst)), "l"((unsigned long long)map), "r"(x), "r"(y), "r"(z), "r"(smem_u32(bar)), "h"(mask)
+        : "memory");
+}
+
+__device__ __forceinline__ void cluster_sync()
+{
+    asm volatile("barrier.cluster.arrive.release.aligned;\nbarrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
+
+__device__ __forceinline__ uint32_t cluster_rank()
+{
+    uint32_t r;
+    asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+    return r;
+}
+
 // tcgen05 shared-memory matrix descriptor: K-major, 128-byte swizzle, 8-row
 // groups 1024 bytes apart (stride byte offset), descriptor version 1.
 __device__ __forceinline__ unsigned long long smem_desc(const void* p)
@@ -208,6 +233,14 @@ __device__ __forceinline__ void mma(uint32_t tmem_d, unsigned long long adesc, u
 __device__ __forceinline__ void mma_commit(unsigned long long* bar)
 {
     asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
+                 : "memory");
+}
+
+// Arrive on `bar` (same offset) in every CTA of `mask` once the prior MMAs complete.
+__device__ __forceinline__ void mma_commit_mc(unsigned long long* bar, uint16_t mask)
+{
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.multicast::cluster.b64 [%0], %1;"
+                 ::"r"(smem_u32(bar)), "h"(mask)
                  : "memory");
 }
 
@@ -271,7 +304,10 @@ struct PassIter {
     }
 };
 
-template <int KIND>
+// CM: CTAs per cluster along M.  The CM CTAs of a cluster own consecutive M-tiles of
+// one N-tile; each loads 1/CM of every B slice tile and multicasts it to all of them,
+// and a B slot is refilled only after every CTA's MMAs released it.
+template <int KIND, int CM>
 __global__ void __launch_bounds__(THREADS, 1)
 gemm_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, const Params p)
 {
@@ -285,17 +321,21 @@ gemm_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
     constexpr int NMMA = 4;                           // MMAs (K=16 bf16 / K=8 tf32) per row
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
 
-    // grouped raster: consecutive CTAs walk group_m M-tiles before the next N-tile
+    // grouped raster over clusters: consecutive clusters walk group_m cluster-rows
+    // (CM M-tiles each) before the next N-tile
+    const int rank = CM > 1 ? (int)cluster_rank() : 0;
+    const int tiles_m2 = (p.tiles_m + CM - 1) / CM;
     const int per_group = p.group_m * p.tiles_n;
-    const int t = blockIdx.x;
+    const int t = blockIdx.x / CM;
     const int first_m = (t / per_group) * p.group_m;
-    const int gm = min(p.tiles_m - first_m, p.group_m);
-    const int m0 = (first_m + (t % per_group) % gm) * BM;
+    const int gm = min(tiles_m2 - first_m, p.group_m);
+    const int m0 = ((first_m + (t % per_group) % gm) * CM + rank) * BM;
     const int n0 = ((t % per_group) / gm) * BN;
+    const uint16_t cmask = (uint16_t)((1u << CM) - 1);
 
     if (threadIdx.x == 0) {
         for (int s = 0; s < NA; ++s) { mbar_init(&ctl->afull[s], 1); mbar_init(&ctl->aempty[s], 1); }
-        for (int s = 0; s < NB; ++s) { mbar_init(&ctl->bfull[s], 1); mbar_init(&ctl->bempty[s], 1); }
+        for (int s = 0; s < NB; ++s) { mbar_init(&ctl->bfull[s], 1); mbar_init(&ctl->bempty[s], CM); }
         for (int b = 0; b < 2; ++b) { mbar_init(&ctl->tfull[b], 1); mbar_init(&ctl->tempty[b], EPI_WARPS); }
         mbar_init(&ctl->drain, 1);
         ctl->abort = 0;
@@ -317,6 +357,7 @@ gemm_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
     }
     fence_before();
     __syncthreads();
+    if (CM > 1) cluster_sync();  // peers' barriers are initialised before any multicast reaches them
     fence_after();
     const uint32_t tmem = ctl->tmem_base;
 
@@ -340,9 +381,10 @@ gemm_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
                     for (int j = lo; j <= hi && ok; ++j) {
                         const int imin = L1 - j > lo ? L1 - j : lo;
                         while (a_here < hi - imin + 1) {
-                            const int as = (int)(a_issued % NA);
-                            if (!mbar_wait(&ctl->aempty[as], (uint32_t)(((a_issued / NA) & 1) ^ 1), ctl, p.status,
-                                           p.wait_ns)) {
+                            const int as = (int)(a_issued & (NA - 1));
+                            const uint32_t par = (uint32_t)(((a_issued / NA) & 1) ^ 1);
+                            if (!mbar_try(&ctl->aempty[as], par) &&
+                                !mbar_wait(&ctl->aempty[as], par, ctl, p.status, p.wait_ns)) {
                                 ok = false;
                                 break;
                             }
@@ -352,14 +394,20 @@ gemm_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
                             ++a_here;
                         }
                         if (!ok) break;
-                        const int bs = (int)(b_issued % NB);
-                        if (!mbar_wait(&ctl->bempty[bs], (uint32_t)(((b_issued / NB) & 1) ^ 1), ctl, p.status,
-                                       p.wait_ns)) {
+                        const int bs = (int)(b_issued & (NB - 1));
+                        const uint32_t bpar = (uint32_t)(((b_issued / NB) & 1) ^ 1);
+                        if (!mbar_try(&ctl->bempty[bs], bpar) &&
+                            !mbar_wait(&ctl->bempty[bs], bpar, ctl, p.status, p.wait_ns)) {
                             ok = false;
                             break;
                         }
                         mbar_expect_tx(&ctl->bfull[bs], B_TILE);
-                        tma_load_3d(bring + bs * B_TILE, &tmB, &ctl->bfull[bs], kb, (int)(p.rowB0 + n0), j);
+                        if (CM == 1) {
+                            tma_load_3d(bring + bs * B_TILE, &tmB, &ctl->bfull[bs], kb, (int)(p.rowB0 + n0), j);
+                        } else {
+                            tma_load_3d_mc(bring + bs * B_TILE + rank * (B_TILE / CM), &tmB, &ctl->bfull[bs], kb,
+                                           (int)(p.rowB0 + n0 + rank * (BN / CM)), j, cmask);
+                        }
                         ++b_issued;
                     }
                 }
@@ -378,10 +426,16 @@ gemm_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
         }
     } else if (warp == 1) {
         // ----------------------------------------------------------------- MMA
+        // Kept lean: the issue loop runs once per B tile (512-1024 cycles of MMA work),
+        // so per-tile bookkeeping uses registers only (no indexed local arrays), slot
+        // descriptors are precomputed and barrier tests take an inline fast path.
         if (lane == 0) {
             const uint32_t idesc = instr_desc<KIND>();
-            long long a_used = 0, b_used = 0;
-            unsigned tuse[2] = {0, 0};
+            // slot q's descriptor = slot 0's + q * tile_bytes / 16 in the start-address field
+            // (shared addresses stay below 256 KB, so the 14-bit field never carries over)
+            const unsigned long long adesc0 = smem_desc(aring), bdesc0 = smem_desc(bring);
+            uint32_t a_used = 0, b_used = 0;
+            uint32_t tuse0 = 0, tuse1 = 0;
             int toggle = 0;
             bool ok = true, any = false;
             PassIter it;
@@ -390,66 +444,76 @@ gemm_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
                 int lo, hi;
                 it.ranges(p, lo, hi);
                 const int L1 = p.glo[it.g], nl = p.gn[it.g], L2 = L1 + nl - 1;
-                int bufs[2], nb;
-                if (nl == 2) { bufs[0] = 0; bufs[1] = 1; nb = 2; }
-                else { bufs[0] = toggle; bufs[1] = toggle; toggle ^= 1; nb = 1; }
-                for (int q = 0; q < nb && ok; ++q)
-                    if (!mbar_wait(&ctl->tempty[bufs[q]], (tuse[bufs[q]] & 1) ^ 1, ctl, p.status, p.wait_ns)) ok = false;
+                // accumulator of level L1 (and L1+1 when the group has two levels)
+                const int buf0 = nl == 2 ? 0 : toggle;
+                const bool use0 = nl == 2 || buf0 == 0, use1 = nl == 2 || buf0 == 1;
+                if (nl == 1) toggle ^= 1;
+                if (use0 && !mbar_try(&ctl->tempty[0], (tuse0 & 1) ^ 1) &&
+                    !mbar_wait(&ctl->tempty[0], (tuse0 & 1) ^ 1, ctl, p.status, p.wait_ns))
+                    ok = false;
+                if (ok && use1 && !mbar_try(&ctl->tempty[1], (tuse1 & 1) ^ 1) &&
+                    !mbar_wait(&ctl->tempty[1], (tuse1 & 1) ^ 1, ctl, p.status, p.wait_ns))
+                    ok = false;
                 if (!ok) break;
                 fence_after();
-                uint32_t acc_on[2] = {0, 0};
+                const uint32_t d0 = tmem + (uint32_t)(buf0 * BN), d1 = tmem + (uint32_t)BN;
+                uint32_t acc_bits = 0;  // bit lv: accumulator of level L1+lv already written this pass
                 for (int kb = it.k0; kb < it.k1 && ok; kb += KSTEP) {
                     int a_wait = 0, a_free = 0;  // A tiles of this K-step waited for / released (i = hi - index)
                     for (int j = lo; j <= hi; ++j) {
                         const int imin = L1 - j > lo ? L1 - j : lo;
                         const int imax = L2 - j < hi ? L2 - j : hi;
                         while (a_wait < hi - imin + 1) {
-                            const long long u = a_used + a_wait;
-                            if (!mbar_wait(&ctl->afull[u % NA], (uint32_t)((u / NA) & 1), ctl, p.status, p.wait_ns)) {
+                            const uint32_t u = a_used + (uint32_t)a_wait;
+                            unsigned long long* bar = &ctl->afull[u & (NA - 1)];
+                            const uint32_t par = (u / NA) & 1;
+                            if (!mbar_try(bar, par) && !mbar_wait(bar, par, ctl, p.status, p.wait_ns)) {
                                 ok = false;
                                 break;
                             }
                             ++a_wait;
                         }
                         if (!ok) break;
-                        const int bs = (int)(b_used % NB);
-                        if (!mbar_wait(&ctl->bfull[bs], (uint32_t)((b_used / NB) & 1), ctl, p.status, p.wait_ns)) {
-                            ok = false;
-                            break;
+                        const int bs = (int)(b_used & (NB - 1));
+                        {
+                            unsigned long long* bar = &ctl->bfull[bs];
+                            const uint32_t par = (b_used / NB) & 1;
+                            if (!mbar_try(bar, par) && !mbar_wait(bar, par, ctl, p.status, p.wait_ns)) {
+                                ok = false;
+                                break;
+                            }
                         }
-                        fence_after();
-                        const unsigned long long bdesc = smem_desc(bring + bs * B_TILE);
+                        const unsigned long long bd = bdesc0 + ((unsigned long long)bs << 11);
                         for (int i = imax; i >= imin; --i) {
                             const int lv = i + j - L1;
-                            const uint32_t d = tmem + (uint32_t)(bufs[lv] * BN);
-                            const int as = (int)((a_used + (hi - i)) % NA);
-                            const unsigned long long ad = smem_desc(aring + as * A_TILE);
-#pragma unroll
-                            for (int k = 0; k < NMMA; ++k) {
-                                // advance the start address by 32 bytes per MMA K-step
-                                mma<KIND>(d, ad + (unsigned long long)(2 * k), bdesc + (unsigned long long)(2 * k), idesc,
-                                          k == 0 ? acc_on[lv] : 1u);
-                            }
-                            acc_on[lv] = 1;
-                            any = true;
+                            const uint32_t d = lv ? d1 : d0;
+                            const unsigned long long ad =
+                                adesc0 + ((unsigned long long)((a_used + (uint32_t)(hi - i)) & (NA - 1)) << 10);
+                            const uint32_t acc = (acc_bits >> lv) & 1u;
+                            // four MMAs per 128-byte row: advance the start address by 32 bytes each
+                            mma<KIND>(d, ad, bd, idesc, acc);
+                            mma<KIND>(d, ad + 2, bd + 2, idesc, 1u);
+                            mma<KIND>(d, ad + 4, bd + 4, idesc, 1u);
+                            mma<KIND>(d, ad + 6, bd + 6, idesc, 1u);
+                            acc_bits |= 1u << lv;
                         }
-                        mma_commit(&ctl->bempty[bs]);
+                        any = true;
+                        if (CM == 1) mma_commit(&ctl->bempty[bs]);
+                        else mma_commit_mc(&ctl->bempty[bs], cmask);
                         ++b_used;
                         // release the A tiles no later B of this K-step needs: i > min(hi, L2 - j - 1)
                         const int keep = j < hi ? (L2 - j - 1 < hi ? L2 - j - 1 : hi) : lo - 1;
                         while (a_free < hi - keep) {
-                            mma_commit(&ctl->aempty[(a_used + a_free) % NA]);
+                            mma_commit(&ctl->aempty[(a_used + (uint32_t)a_free) & (NA - 1)]);
                             ++a_free;
                         }
                     }
                     if (!ok) break;
-                    a_used += hi - lo + 1;
+                    a_used += (uint32_t)(hi - lo + 1);
                 }
                 if (!ok) break;
-                for (int q = 0; q < nb; ++q) {
-                    mma_commit(&ctl->tfull[bufs[q]]);
-                    ++tuse[bufs[q]];
-                }
+                if (use0) { mma_commit(&ctl->tfull[0]); ++tuse0; }
+                if (use1) { mma_commit(&ctl->tfull[1]); ++tuse1; }
             } while (it.next(p));
             if (!ok && any) {
                 mma_commit(&ctl->drain);
@@ -461,18 +525,20 @@ gemm_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
         const int q4 = warp & 3;  // TMEM lane quarter this warp may access
         const int row0 = q4 * 32;
         float(*stg)[33] = ctl->stage[warp - 2];
-        unsigned tuse[2] = {0, 0};
+        uint32_t tuse0 = 0, tuse1 = 0;
         int toggle = 0;
         PassIter it;
         it.begin(p);
         bool ok = true;
         do {
             const int L1 = p.glo[it.g], nl = p.gn[it.g];
-            int bufs[2], nb;
-            if (nl == 2) { bufs[0] = 0; bufs[1] = 1; nb = 2; }
-            else { bufs[0] = toggle; bufs[1] = toggle; toggle ^= 1; nb = 1; }
-            for (int q = 0; q < nb && ok; ++q)
-                if (!mbar_wait(&ctl->tfull[bufs[q]], tuse[bufs[q]] & 1, ctl, p.status, p.wait_ns)) ok = false;
+            // buffer of level L1 + q is (q ? 1 : buf0)
+            const int buf0 = nl == 2 ? 0 : toggle;
+            const int nb = nl;
+            const bool use0 = nl == 2 || buf0 == 0, use1 = nl == 2 || buf0 == 1;
+            if (nl == 1) toggle ^= 1;
+            if (use0 && !mbar_wait(&ctl->tfull[0], tuse0 & 1, ctl, p.status, p.wait_ns)) ok = false;
+            if (ok && use1 && !mbar_wait(&ctl->tfull[1], tuse1 & 1, ctl, p.status, p.wait_ns)) ok = false;
             if (!ok) break;
             fence_after();
             const bool first = it.idx == 0, last = it.last(p);
@@ -486,7 +552,7 @@ gemm_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
                     for (int r = 0; r < 32; ++r) X[r] = 0;
                     for (int q = 0; q < nb; ++q) {
                         float v[32];
-                        tmem_ld32(tmem + ((uint32_t)row0 << 16) + (uint32_t)(bufs[q] * BN + c * 32), v);
+                        tmem_ld32(tmem + ((uint32_t)row0 << 16) + (uint32_t)((q ? 1 : buf0) * BN + c * 32), v);
 #pragma unroll
                         for (int j = 0; j < 32; ++j) stg[lane][j] = v[j];
                         __syncwarp();
@@ -527,7 +593,7 @@ gemm_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
                 } else {
                     for (int q = 0; q < nb; ++q) {
                         float v[32];
-                        tmem_ld32(tmem + ((uint32_t)row0 << 16) + (uint32_t)(bufs[q] * BN + c * 32), v);
+                        tmem_ld32(tmem + ((uint32_t)row0 << 16) + (uint32_t)((q ? 1 : buf0) * BN + c * 32), v);
 #pragma unroll
                         for (int j = 0; j < 32; ++j) stg[lane][j] = v[j];
                         __syncwarp();
@@ -551,14 +617,18 @@ gemm_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
             }
             fence_before();
             __syncwarp();
-            if (lane == 0)
-                for (int q = 0; q < nb; ++q) mbar_arrive(&ctl->tempty[bufs[q]]);
-            for (int q = 0; q < nb; ++q) ++tuse[bufs[q]];
+            if (lane == 0) {
+                if (use0) mbar_arrive(&ctl->tempty[0]);
+                if (use1) mbar_arrive(&ctl->tempty[1]);
+            }
+            if (use0) ++tuse0;
+            if (use1) ++tuse1;
         } while (it.next(p));
     }
 
     fence_before();
     __syncthreads();
+    if (CM > 1) cluster_sync();  // no CTA leaves while a peer may still multicast into it
     fence_after();
     if (warp == 1) {
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TMEM_COLS));
@@ -627,26 +697,41 @@ cudaError_t gemm_tc(const GemmTc& g, cudaStream_t s)
     p.wait_ns = g.wait_ns;
     p.tiles_m = (g.M + BM - 1) / BM;
     p.tiles_n = (g.N + BN - 1) / BN;
-    p.group_m = p.tiles_m < 16 ? p.tiles_m : 16;
+    const int CM = p.tiles_m >= 2 ? 2 : 1;
+    const int tiles_m2 = (p.tiles_m + CM - 1) / CM;
+    p.group_m = tiles_m2 < 8 ? tiles_m2 : 8;
     CUtensorMap ma, mb;
     if (!make_map(&ma, g.A, g.kind, g.K, g.pitchA, g.rowsA, g.slices, BM)) return cudaErrorInvalidValue;
-    if (!make_map(&mb, g.B, g.kind, g.K, g.pitchB, g.rowsB, g.slices, BN)) return cudaErrorInvalidValue;
-    const long long ntiles = (long long)p.tiles_m * p.tiles_n;
-    if (ntiles > 0x7fffffffll) return cudaErrorInvalidConfiguration;
-    static bool attr_done[2] = {false, false};
-    if (g.kind == TC_BF16) {
-        if (!attr_done[0]) {
-            cudaFuncSetAttribute(gemm_tc_kernel<TC_BF16>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SMEM_BYTES);
-            attr_done[0] = true;
-        }
-        gemm_tc_kernel<TC_BF16><<<(unsigned)ntiles, THREADS, SMEM_BYTES, s>>>(ma, mb, p);
-    } else {
-        if (!attr_done[1]) {
-            cudaFuncSetAttribute(gemm_tc_kernel<TC_TF32>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SMEM_BYTES);
-            attr_done[1] = true;
-        }
-        gemm_tc_kernel<TC_TF32><<<(unsigned)ntiles, THREADS, SMEM_BYTES, s>>>(ma, mb, p);
-    }
+    if (!make_map(&mb, g.B, g.kind, g.K, g.pitchB, g.rowsB, g.slices, BN / CM)) return cudaErrorInvalidValue;
+    const long long nctas = (long long)tiles_m2 * CM * p.tiles_n;
+    if (nctas > 0x7fffffffll) return cudaErrorInvalidConfiguration;
+    cudaLaunchConfig_t cfg{};
+    cfg.gridDim = dim3((unsigned)nctas);
+    cfg.blockDim = dim3(THREADS);
+    cfg.dynamicSmemBytes = SMEM_BYTES;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = CM;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = CM > 1 ? 1 : 0;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        cudaFuncSetAttribute(gemm_tc_kernel<TC_BF16, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SMEM_BYTES);
+        cudaFuncSetAttribute(gemm_tc_kernel<TC_BF16, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SMEM_BYTES);
+        cudaFuncSetAttribute(gemm_tc_kernel<TC_TF32, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SMEM_BYTES);
+        cudaFuncSetAttribute(gemm_tc_kernel<TC_TF32, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SMEM_BYTES);
+    });
+    cudaError_t err;
+    if (g.kind == TC_BF16)
+        err = CM == 2 ? cudaLaunchKernelEx(&cfg, gemm_tc_kernel<TC_BF16, 2>, ma, mb, p)
+                      : cudaLaunchKernelEx(&cfg, gemm_tc_kernel<TC_BF16, 1>, ma, mb, p);
+    else
+        err = CM == 2 ? cudaLaunchKernelEx(&cfg, gemm_tc_kernel<TC_TF32, 2>, ma, mb, p)
+                      : cudaLaunchKernelEx(&cfg, gemm_tc_kernel<TC_TF32, 1>, ma, mb, p);
+    if (err != cudaSuccess) return err;
     count_launch();
     return cudaGetLastError();
 }
