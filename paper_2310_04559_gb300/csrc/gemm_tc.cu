@@ -43,6 +43,7 @@
 #include <cudaTypedefs.h>
 #include <cuda_runtime.h>
 
+#include <cstdlib>
 #include <mutex>
 
 #include "cc_internal.cuh"
@@ -697,7 +698,14 @@ cudaError_t gemm_tc(const GemmTc& g, cudaStream_t s)
     p.wait_ns = g.wait_ns;
     p.tiles_m = (g.M + BM - 1) / BM;
     p.tiles_n = (g.N + BN - 1) / BN;
-    const int CM = p.tiles_m >= 2 ? 2 : 1;
+    // CTAs per cluster along M (B multicast).  Measured on GB300 at o40/v400/n2000 the
+    // multicast costs more in coupling than it saves in L2 traffic (65.8 vs 63.6 TFLOP/s),
+    // so it is off unless CC_LADDER_TC_CLUSTER=2.
+    static const int cluster_pref = [] {
+        const char* e = getenv("CC_LADDER_TC_CLUSTER");
+        return (e && e[0] == '2') ? 2 : 1;
+    }();
+    const int CM = (p.tiles_m >= 2 && cluster_pref == 2) ? 2 : 1;
     const int tiles_m2 = (p.tiles_m + CM - 1) / CM;
     p.group_m = tiles_m2 < 8 ? tiles_m2 : 8;
     CUtensorMap ma, mb;
