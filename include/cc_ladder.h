@@ -143,6 +143,16 @@ int cc_ladder_fwd(int o, int v, int n_chol, const double* L, const double* t2, d
 /* Forward with every option (order, a-block, accumulate, pair symmetry, exchange, slices). */
 int cc_ladder_fwd_ex(const cc_ladder_args* args);
 
+/* Autotuner: times both contraction orders (Section 3.2) on this shape with the caller's
+ * buffers and workspace (one and two blocks of `a` per order, extrapolated to all blocks), and
+ * records the faster one for (o, v, n_chol, mode, symmetric/exchange flags).  Later calls with
+ * order = CC_ORDER_AUTO use the recorded order; without a record they use the flop cost model.
+ * If the environment variable CC_LADDER_CACHE names a file, records are appended to it and read
+ * back by later processes.  R (and only R) is overwritten with partial results.  Synchronous.
+ * plan (nullable) receives the chosen plan; ms_if / ms_cf (nullable) the estimated milliseconds
+ * of each order (-1 where the order does not fit the workspace). */
+int cc_ladder_autotune(const cc_ladder_args* args, cc_ladder_plan* plan, double* ms_if, double* ms_cf);
+
 /* Workspace bytes for cc_ladder_bwd. */
 int cc_ladder_bwd_workspace_size(int o, int v, int n_chol, int mode, size_t budget_bytes, size_t* bytes);
 

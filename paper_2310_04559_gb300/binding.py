@@ -99,6 +99,32 @@ def plan(o, v, n, ws_bytes=0, **kw) -> dict:
             "flops_algorithmic": p.flops_algorithmic, "flops_issued": p.flops_issued}
 
 
+def autotune(L, t2, R=None, mode="ozaki_bf16", symmetric=False, exchange=False, slices=0, budget=0,
+             workspace=None) -> dict:
+    """Time both contraction orders on this shape and record the faster one for
+    order="auto"; returns the chosen plan and the per-order estimates (ms)."""
+    lib = _lib.load()
+    o, v, n = _shapes(L, t2)
+    _check_tensor(L, "L", (n, v, v))
+    _check_tensor(t2, "t2", (o, o, v, v))
+    R = torch.empty_like(t2) if R is None else R
+    a = make_args(o, v, n, mode, "auto", symmetric, exchange, False, 0, slices, budget)
+    if workspace is None:
+        # big enough for either order under the budget
+        ws = max(workspace_size(o, v, n, mode=mode, order=od, symmetric=symmetric, exchange=exchange,
+                                slices=slices, budget=budget) for od in ("integral_first", "cholesky_first"))
+        workspace = alloc_workspace(ws, L.device)
+    a.L, a.t2, a.R = _ptr(L), _ptr(t2), _ptr(R)
+    a.workspace, a.ws_bytes = _ptr(workspace), workspace.numel()
+    a.stream = _stream(L.device)
+    p = _lib.Plan()
+    t_if, t_cf = ctypes.c_double(), ctypes.c_double()
+    _lib.check(lib.cc_ladder_autotune(ctypes.byref(a), ctypes.byref(p), ctypes.byref(t_if), ctypes.byref(t_cf)),
+               "cc_ladder_autotune")
+    return {"order": {1: "integral_first", 2: "cholesky_first"}[p.order], "a_block": p.a_block,
+            "ms_integral_first": t_if.value, "ms_cholesky_first": t_cf.value}
+
+
 def alloc_workspace(nbytes: int, device) -> torch.Tensor:
     return torch.empty(max(int(nbytes), 256), dtype=torch.uint8, device=device)
 

@@ -17,6 +17,10 @@
 
 #include <algorithm>
 #include <atomic>
+#include <cstdio>
+#include <cstdlib>
+#include <map>
+#include <tuple>
 #include <cmath>
 #include <cstdint>
 #include <cstring>
@@ -122,9 +126,63 @@ struct BwdLayout {
 double flops_if(const Ctx& c) { return 2.0 * ((double)c.pairs + c.n) * std::pow((double)c.v, 4); }
 double flops_cf(const Ctx& c) { return 4.0 * c.n * (double)c.pairs * std::pow((double)c.v, 3); }
 
+// ---------------------------------------------------------------- autotuner
+// Orders decided by timed trials (cc_ladder_autotune), per shape and mode; also kept
+// in a text file when CC_LADDER_CACHE names one ("o v n mode flags order" per line).
+struct TuneKey {
+    int o, v, n, mode, flags;
+    bool operator<(const TuneKey& b) const
+    {
+        return std::tie(o, v, n, mode, flags) < std::tie(b.o, b.v, b.n, b.mode, b.flags);
+    }
+};
+std::mutex g_tune_mu;
+std::map<TuneKey, int> g_tuned;
+bool g_cache_loaded = false;
+
+int tune_flags(int flags) { return flags & (CC_FLAG_SYMMETRIC_T | CC_FLAG_EXCHANGE); }
+
+void load_cache_locked()
+{
+    if (g_cache_loaded) return;
+    g_cache_loaded = true;
+    const char* path = getenv("CC_LADDER_CACHE");
+    if (!path || !*path) return;
+    FILE* f = fopen(path, "r");
+    if (!f) return;
+    TuneKey k;
+    int order;
+    while (fscanf(f, "%d %d %d %d %d %d", &k.o, &k.v, &k.n, &k.mode, &k.flags, &order) == 6)
+        if (order == CC_ORDER_INTEGRAL_FIRST || order == CC_ORDER_CHOLESKY_FIRST) g_tuned[k] = order;
+    fclose(f);
+}
+
+int cached_order(const TuneKey& k)
+{
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    load_cache_locked();
+    auto it = g_tuned.find(k);
+    return it == g_tuned.end() ? 0 : it->second;
+}
+
+void store_order(const TuneKey& k, int order)
+{
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    load_cache_locked();
+    g_tuned[k] = order;
+    const char* path = getenv("CC_LADDER_CACHE");
+    if (path && *path) {
+        if (FILE* f = fopen(path, "a")) {
+            fprintf(f, "%d %d %d %d %d %d\n", k.o, k.v, k.n, k.mode, k.flags, order);
+            fclose(f);
+        }
+    }
+}
+
 int pick_order(const Ctx& c, int requested)
 {
     if (requested == CC_ORDER_INTEGRAL_FIRST || requested == CC_ORDER_CHOLESKY_FIRST) return requested;
+    if (const int t = cached_order(TuneKey{c.o, c.v, c.n, c.mode, tune_flags(c.flags)})) return t;
     // Cost model: tensor-core flops, with the Cholesky-first order charged for its
     // larger intermediate traffic (it writes and re-reads o^2 n v^2 per block).
     const double cf = flops_cf(c) * 1.15, itf = flops_if(c);
@@ -696,6 +754,65 @@ int cc_ladder_plan_query(const cc_ladder_args* args, cc_ladder_plan* plan)
 }
 
 int cc_ladder_fwd_ex(const cc_ladder_args* args) { return fwd_impl(args); }
+
+int cc_ladder_autotune(const cc_ladder_args* args, cc_ladder_plan* plan, double* ms_if, double* ms_cf)
+{
+    Ctx c;
+    CC_TRY(make_ctx(args, &c));
+    if (!args->L || !args->t2 || !args->R || !args->workspace) return CC_ERR_NULL;
+    cudaStream_t st = (cudaStream_t)args->stream;
+    const int orders[2] = {CC_ORDER_INTEGRAL_FIRST, CC_ORDER_CHOLESKY_FIRST};
+    double est[2] = {-1.0, -1.0};
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) return CC_ERR_CUDA;
+    int status = CC_OK;
+    for (int q = 0; q < 2 && status == CC_OK; ++q) {
+        cc_ladder_args a = *args;
+        a.order = orders[q];
+        a.energy = nullptr;
+        a.flags &= ~CC_FLAG_ACCUMULATE;
+        Ctx cq;
+        make_ctx(&a, &cq);
+        size_t need = 0;
+        const int A = pick_block(cq, a.ws_bytes, a.a_block, &need);
+        if (A < 0) continue;  // this order does not fit the workspace
+        // time one block and (when there is one) two blocks: fixed cost + per-block cost
+        double t[2] = {0.0, 0.0};
+        const int nb = (c.v + A - 1) / A;
+        const int reps = nb >= 2 ? 2 : 1;
+        for (int r = 0; r < reps && status == CC_OK; ++r) {
+            a.a_lo = 0;
+            a.a_hi = std::min(c.v, (r + 1) * A);
+            status = fwd_impl(&a);  // warm (first use of the shape)
+            if (status != CC_OK) break;
+            cudaEventRecord(e0, st);
+            status = fwd_impl(&a);
+            cudaEventRecord(e1, st);
+            if (status != CC_OK) break;
+            cudaEventSynchronize(e1);
+            float ms = 0.f;
+            cudaEventElapsedTime(&ms, e0, e1);
+            t[r] = ms;
+        }
+        if (status != CC_OK) break;
+        est[q] = reps == 2 ? t[0] + (nb - 1) * (t[1] - t[0]) : t[0];
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (status != CC_OK) return status;
+    if (est[0] < 0 && est[1] < 0) return CC_ERR_WORKSPACE;
+    const int best = (est[1] >= 0 && (est[0] < 0 || est[1] < est[0])) ? orders[1] : orders[0];
+    store_order(TuneKey{c.o, c.v, c.n, c.mode, tune_flags(c.flags)}, best);
+    if (ms_if) *ms_if = est[0];
+    if (ms_cf) *ms_cf = est[1];
+    if (plan) {
+        cc_ladder_args a = *args;
+        a.order = best;
+        a.a_lo = a.a_hi = 0;
+        return cc_ladder_plan_query(&a, plan);
+    }
+    return CC_OK;
+}
 
 int cc_ladder_fwd(int o, int v, int n_chol, const double* L, const double* t2, double* R, int mode, double* energy,
                   void* workspace, size_t ws_bytes, void* stream)

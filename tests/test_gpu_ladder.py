@@ -174,3 +174,61 @@ def test_adjoint_autograd_identities(dev):
     lv = float(loss)
     assert abs(float((tg.grad * tg).sum()) - lv) < 1e-11 * abs(lv)
     assert abs(float((Lg.grad * Lg).sum()) - 2 * lv) < 1e-11 * abs(lv)
+
+
+def test_adjoint_workload_o16_v160_n800(dev, oracle):
+    """Full-size adjoint workload in FP64 through the autograd.Function: sampled
+    gradient entries against the oracle computed one by one, directional central
+    finite differences (h = 1e-6; the loss is linear in t2 and quadratic in L, so
+    central differences are exact up to rounding), and the emulated-FP64 adjoint."""
+    o, v, n = 16, 160, 800
+    L, t2 = synth.ladder_inputs(o, v, n, seed=4)
+    W = synth.cotangent(o, v, seed=5)
+    Wg = cu(W, dev)
+    Lg, tg = cu(L, dev).requires_grad_(), cu(t2, dev).requires_grad_()
+    R = B.ladder(Lg, tg, mode="fp64", symmetric=True)
+    (R * Wg).sum().backward()
+    dL, dt2 = Lg.grad.detach(), tg.grad.detach()
+    rng = np.random.default_rng(6)
+    i1 = rng.integers(0, t2.size, 24)
+    i2 = rng.integers(0, L.size, 24)
+    e1, e2 = oracle.ladder_grad_entries(L, t2, W, i1, i2)
+    assert np.allclose(dt2.cpu().numpy().ravel()[i1], e1, rtol=1e-11, atol=1e-13 * np.abs(e1).max())
+    assert np.allclose(dL.cpu().numpy().ravel()[i2], e2, rtol=1e-11, atol=1e-13 * np.abs(e2).max())
+
+    def loss(Lx, tx):
+        return float((B.ladder_forward(Lx, tx, mode="fp64", symmetric=True) * Wg).sum())
+
+    h = 1e-6
+    Lc, tc = cu(L, dev), cu(t2, dev)
+    for seed in (7, 8):
+        DL = cu(np.random.default_rng(seed).standard_normal(L.shape), dev)
+        fd = (loss(Lc + h * DL, tc) - loss(Lc - h * DL, tc)) / (2 * h)
+        an = float((dL * DL).sum())
+        assert abs(fd - an) <= 1e-6 * abs(an)
+        Dt = cu(synth.amplitudes(o, v, rng=np.random.default_rng(seed + 10), sigma=1.0), dev)
+        fd = (loss(Lc, tc + h * Dt) - loss(Lc, tc - h * Dt)) / (2 * h)
+        an = float((dt2 * Dt).sum())
+        assert abs(fd - an) <= 1e-6 * abs(an)
+    # emulated FP64 adjoint agrees with the FP64 one
+    dLz, dtz = B.ladder_backward(Lc, tc, Wg, mode="ozaki_bf16", symmetric=True)
+    assert rel(dtz.cpu().numpy(), dt2.cpu().numpy()) < 1e-10
+    assert rel(dLz.cpu().numpy(), dL.cpu().numpy()) < 1e-10
+
+
+@pytest.mark.parametrize("mode", ["fp64", "ozaki_bf16"])
+def test_a_range_shards_assemble(dev, mode):
+    """Disjoint a-ranges (one per device in a multi-GPU run) write disjoint entries;
+    their sum is the full R, with and without pair symmetry."""
+    o, v, n = 4, 45, 70
+    L, t2 = synth.ladder_inputs(o, v, n, seed=12)
+    Lg, tg = cu(L, dev), cu(t2, dev)
+    for sym in (False, True):
+        full = B.ladder_forward(Lg, tg, mode=mode, symmetric=sym)
+        parts = torch.zeros_like(full)
+        for lo, hi in [(0, 13), (13, 30), (30, 45)]:
+            Rp = torch.zeros_like(full)
+            B.ladder_forward(Lg, tg, R=Rp, mode=mode, symmetric=sym, a_range=(lo, hi))
+            # nothing outside this range's share is written
+            parts += Rp
+        assert rel(parts.cpu().numpy(), full.cpu().numpy()) < 1e-14
