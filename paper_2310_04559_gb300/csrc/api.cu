@@ -36,6 +36,7 @@ constexpr int kDefaultSlices = 6;
 constexpr int kBeta = 7;                 // bits per Ozaki slice (balanced digits in [-64, 64])
 constexpr int kMixedChunk = 16384;       // K elements per FP32 accumulation in the BF16 / TF32 modes
 constexpr int kFixF = 26;                // fixed-point fraction bits (of a level-0 unit) in the Ozaki epilogue
+constexpr int kFixedBase = 2 - 2 * kBeta - kFixF;  // exponent of one fixed-point unit, before row/col exponents
 constexpr size_t kDefaultBudget = 150ull << 30;
 
 std::atomic<unsigned long long> g_wait_ns{2000000000ull};
@@ -284,7 +285,6 @@ int prep_fixed(const Ctx& c, const FixedSrc& src, Operand& op, cudaStream_t st)
     return check_cuda(split_fixed_rows_bf16(src, c.s, kBeta, op.D, op.pitch, op.e, st));
 }
 
-constexpr int kFixedBase = 2 - 2 * kBeta - kFixF;  // exponent of one fixed-point unit, before row/col exponents
 
 int prep_cols(const Ctx& c, const ColSrc& src, Operand& op, unsigned long long* colmax, cudaStream_t st)
 {
@@ -325,6 +325,23 @@ int run_tc(const char* name, const Ctx& c, int M, int N, int K, const Operand& A
         }
         g.epi = out.accumulate ? EPI_FP64_RMW : (intermediate ? EPI_FIXED64_RED : EPI_FIXED64);
         g.fixF = kFixF;
+        // Final outputs with few tiles: split K so the CTAs fill whole waves (int64 adds,
+        // then one conversion pass).
+        if (g.epi == EPI_FIXED64) {
+            const long long tiles = (long long)((M + 127) / 128) * ((N + 255) / 256);
+            const int nsm = device_sm_count();
+            auto eff = [&](int S) {
+                const double w = (double)tiles * S / nsm;
+                return w / std::ceil(w);
+            };
+            int best = 1;
+            for (int S = 2; S <= 8 && (long long)K / S >= 8192; ++S)
+                if (eff(S) > eff(best) + 0.02) best = S;
+            if (best > 1) {
+                g.epi = EPI_FIXED64_ADD;
+                g.ksplit = best;
+            }
+        }
     } else {
         g.ngroups = 1;
         g.glo[0] = 0; g.gn[0] = 1; g.gkc[0] = kMixedChunk;
@@ -334,6 +351,11 @@ int run_tc(const char* name, const Ctx& c, int M, int N, int K, const Operand& A
     g.out = out;
     g.status = status;
     g.wait_ns = g_wait_ns.load();
+    if (g.epi == EPI_FIXED64_ADD) {
+        CC_CU(zero_out(M, N, out, st));
+        CC_CU(gemm_tc(g, st));
+        return check_cuda(fixed_to_f64(M, N, out, A.e, rowA0, B.e, rowB0, kFixedBase, st));
+    }
     return check_cuda(gemm_tc(g, st));
 }
 

@@ -65,7 +65,7 @@ cudaError_t gemm_f64(const GemmF64& g, cudaStream_t s);
 // after every pass (EPI_FP64_RMW) or summed exactly as int64 fixed point with
 // 2^-fixF resolution of a level-0 unit and converted once (EPI_FIXED64).
 enum TcKind { TC_BF16 = 0, TC_TF32 = 1 };
-enum TcEpi { EPI_FP64_RMW = 0, EPI_FIXED64 = 1, EPI_FIXED64_RED = 2 };
+enum TcEpi { EPI_FP64_RMW = 0, EPI_FIXED64 = 1, EPI_FIXED64_RED = 2, EPI_FIXED64_ADD = 3 };
 constexpr int kMaxGroups = 8;
 
 struct GemmTc {
@@ -81,12 +81,19 @@ struct GemmTc {
     int gn[kMaxGroups];         // levels in the group (1 or 2)
     int gkc[kMaxGroups];        // K elements per pass (0 = whole K; else a multiple of 64 bf16 / 32 tf32)
     int epi, fixF;              // TcEpi; fixed-point fraction bits for EPI_FIXED64
+    int ksplit;                 // K split across this many CTAs per tile (EPI_FIXED64_ADD only; 1 = none)
     OutDesc out;
     int* status;                // device status word (bit 0: wait bound expired)
     unsigned long long wait_ns; // bound on every device-side wait
 };
 cudaError_t gemm_tc(const GemmTc& g, cudaStream_t s);
 int tc_gemm_available();
+int device_sm_count();
+// C[rmap(m) + cmap(n)] (int64 fixed point) -> FP64: X * 2^(eA[rowA0+m] + eB[rowB0+n] + base)
+cudaError_t fixed_to_f64(int M, int N, const OutDesc& out, const int* eA, long long rowA0, const int* eB,
+                         long long rowB0, int base, cudaStream_t s);
+// C[rmap(m) + cmap(n)] = 0 (as int64) for m < M, n < N
+cudaError_t zero_out(int M, int N, const OutDesc& out, cudaStream_t s);
 
 // ------------------------------------------------------------------- splitting
 // Row source: X(r, k) = X[rm(r) + km(k)], k contiguous (km.s1 == 1 for the inner level).

@@ -26,6 +26,8 @@
 //   FIXED64_RED  as FIXED64 but the output stays int64 fixed point: the first pass
 //            stores, later passes add with red.global (no loads in the epilogue); the
 //            split kernel that consumes the intermediate applies the exponents.
+//   FIXED64_ADD  split-K: every pass of every CTA adds with red.global into an int64
+//            tile zeroed beforehand; fixed_to_f64 converts it afterwards.
 //   FP64RMW  every pass adds 2^e * acc into the FP64 output (mixed modes, and
 //            accumulation into caller data).  Single-level passes alternate the
 //            two accumulators so the MMAs of pass p+1 overlap the drain of pass p.
@@ -86,6 +88,7 @@ struct Params {
     int ngroups;
     int glo[kMaxGroups], gn[kMaxGroups], gkc[kMaxGroups];
     int epi, fixF;
+    int ksplit, kper;            // K split: CTA split s owns [s*kper, min(K, (s+1)*kper))
     int tiles_m, tiles_n, group_m;
     OutDesc out;
     int* status;
@@ -277,25 +280,31 @@ __device__ __forceinline__ long long fix_shift(int q, int sh)
     return ((long long)q + (1ll << (-sh - 1))) >> (-sh);
 }
 
-// Pass sequence shared by all roles: groups in order, each cut into K-chunks.
+// Pass sequence shared by all roles: groups in order, each cut into K-chunks, over
+// this CTA's K range [kbeg, kend).
 struct PassIter {
-    int g, k0, k1, idx;
+    int g, k0, k1, idx, kbeg, kend;
     __device__ int chunk_end(const Params& p, int from) const
     {
         const int kc = p.gkc[g];
-        return (kc > 0 && from + kc < p.K) ? from + kc : p.K;
+        return (kc > 0 && from + kc < kend) ? from + kc : kend;
     }
-    __device__ void begin(const Params& p) { g = 0; k0 = 0; k1 = chunk_end(p, 0); idx = 0; }
+    __device__ void begin(const Params& p, int split)
+    {
+        kbeg = split * p.kper;
+        kend = min(p.K, kbeg + p.kper);
+        g = 0; k0 = kbeg; k1 = chunk_end(p, kbeg); idx = 0;
+    }
     __device__ bool next(const Params& p)
     {
         ++idx;
-        if (k1 < p.K) { k0 = k1; k1 = chunk_end(p, k0); return true; }
+        if (k1 < kend) { k0 = k1; k1 = chunk_end(p, k0); return true; }
         if (++g >= p.ngroups) return false;
-        k0 = 0;
-        k1 = chunk_end(p, 0);
+        k0 = kbeg;
+        k1 = chunk_end(p, kbeg);
         return true;
     }
-    __device__ bool last(const Params& p) const { return k1 >= p.K && g == p.ngroups - 1; }
+    __device__ bool last(const Params& p) const { return k1 >= kend && g == p.ngroups - 1; }
     // slice index range whose products land in the group's levels
     __device__ void ranges(const Params& p, int& lo, int& hi) const
     {
@@ -327,7 +336,9 @@ gemm_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
     const int rank = CM > 1 ? (int)cluster_rank() : 0;
     const int tiles_m2 = (p.tiles_m + CM - 1) / CM;
     const int per_group = p.group_m * p.tiles_n;
-    const int t = blockIdx.x / CM;
+    const int nclus = tiles_m2 * p.tiles_n;             // clusters per K split
+    const int split = (int)(blockIdx.x / CM) / nclus;    // this CTA's K split
+    const int t = (int)(blockIdx.x / CM) % nclus;
     const int first_m = (t / per_group) * p.group_m;
     const int gm = min(tiles_m2 - first_m, p.group_m);
     const int m0 = ((first_m + (t % per_group) % gm) * CM + rank) * BM;
@@ -372,7 +383,7 @@ gemm_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
             long long a_issued = 0, b_issued = 0;
             bool ok = true;
             PassIter it;
-            it.begin(p);
+            it.begin(p, split);
             do {
                 int lo, hi;
                 it.ranges(p, lo, hi);
@@ -440,7 +451,7 @@ gemm_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
             int toggle = 0;
             bool ok = true, any = false;
             PassIter it;
-            it.begin(p);
+            it.begin(p, split);
             do {
                 int lo, hi;
                 it.ranges(p, lo, hi);
@@ -529,7 +540,7 @@ gemm_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
         uint32_t tuse0 = 0, tuse1 = 0;
         int toggle = 0;
         PassIter it;
-        it.begin(p);
+        it.begin(p, split);
         bool ok = true;
         do {
             const int L1 = p.glo[it.g], nl = p.gn[it.g];
@@ -563,14 +574,16 @@ gemm_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
                         __syncwarp();
                     }
                     const int eb = ctl->eB[c * 32 + lane] + p.scale_base - p.fixF;
-                    if (p.epi == EPI_FIXED64_RED) {
-                        // int64 result for a consumer that scales it: store, then add without reading
+                    if (p.epi == EPI_FIXED64_RED || p.epi == EPI_FIXED64_ADD) {
+                        // int64 result for a consumer that scales it: store (first pass of an
+                        // unsplit tile), then add without reading
+                        const bool store = first && p.epi == EPI_FIXED64_RED;
 #pragma unroll
                         for (int r = 0; r < 32; ++r) {
                             const long long ro = ctl->rowoff[row0 + r];
                             if (ro < 0 || !ncol) continue;
                             unsigned long long* dst = (unsigned long long*)(p.out.C + ro + co);
-                            if (first) __stcg((long long*)dst, X[r]);
+                            if (store) __stcg((long long*)dst, X[r]);
                             else atomicAdd(dst, (unsigned long long)X[r]);
                         }
                         continue;
@@ -672,6 +685,53 @@ bool make_map(CUtensorMap* m, const void* base, int kind, long long K, long long
 
 int tc_gemm_available() { return get_encode() != nullptr; }
 
+int device_sm_count()
+{
+    int dev = 0, n = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return 148;
+    if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n <= 0) return 148;
+    return n;
+}
+
+namespace {
+__global__ void fixed_to_f64_kernel(int M, int N, const OutDesc out, const int* __restrict__ eA, long long rowA0,
+                                    const int* __restrict__ eB, long long rowB0, int base, int zero)
+{
+    const int n = blockIdx.x * blockDim.x + threadIdx.x;
+    if (n >= N) return;
+    const long long co = map2(out.cmap, n);
+    const int en = (eB ? eB[rowB0 + n] : 0) + base;
+    for (int m = blockIdx.y; m < M; m += gridDim.y) {
+        double* dst = out.C + map2(out.rmap, m) + co;
+        if (zero) {
+            *(long long*)dst = 0;
+        } else {
+            const long long X = *(const long long*)dst;
+            *dst = (double)X * pow2((eA ? eA[rowA0 + m] : 0) + en);
+        }
+    }
+}
+}  // namespace
+
+cudaError_t zero_out(int M, int N, const OutDesc& out, cudaStream_t s)
+{
+    if (M <= 0 || N <= 0) return cudaSuccess;
+    fixed_to_f64_kernel<<<dim3((N + 255) / 256, M < 65535 ? M : 65535), 256, 0, s>>>(M, N, out, nullptr, 0, nullptr, 0,
+                                                                                     0, 1);
+    count_launch();
+    return cudaGetLastError();
+}
+
+cudaError_t fixed_to_f64(int M, int N, const OutDesc& out, const int* eA, long long rowA0, const int* eB,
+                         long long rowB0, int base, cudaStream_t s)
+{
+    if (M <= 0 || N <= 0) return cudaSuccess;
+    fixed_to_f64_kernel<<<dim3((N + 255) / 256, M < 65535 ? M : 65535), 256, 0, s>>>(M, N, out, eA, rowA0, eB, rowB0,
+                                                                                     base, 0);
+    count_launch();
+    return cudaGetLastError();
+}
+
 cudaError_t gemm_tc(const GemmTc& g, cudaStream_t s)
 {
     if (g.M <= 0 || g.N <= 0) return cudaSuccess;
@@ -693,6 +753,11 @@ cudaError_t gemm_tc(const GemmTc& g, cudaStream_t s)
     if (g.epi != EPI_FP64_RMW && g.out.accumulate) return cudaErrorInvalidValue;
     p.epi = g.epi;
     p.fixF = g.fixF;
+    p.ksplit = g.ksplit > 1 ? g.ksplit : 1;
+    if (p.ksplit > 1 && g.epi != EPI_FIXED64_ADD) return cudaErrorInvalidValue;
+    p.kper = (int)((((long long)g.K + p.ksplit - 1) / p.ksplit + kstep - 1) / kstep * kstep);
+    for (int i = 0; i < g.ngroups; ++i)
+        if (p.ksplit > 1 && g.gkc[i] != 0) return cudaErrorInvalidValue;
     p.out = g.out;
     p.status = g.status;
     p.wait_ns = g.wait_ns;
@@ -711,7 +776,7 @@ cudaError_t gemm_tc(const GemmTc& g, cudaStream_t s)
     CUtensorMap ma, mb;
     if (!make_map(&ma, g.A, g.kind, g.K, g.pitchA, g.rowsA, g.slices, BM)) return cudaErrorInvalidValue;
     if (!make_map(&mb, g.B, g.kind, g.K, g.pitchB, g.rowsB, g.slices, BN / CM)) return cudaErrorInvalidValue;
-    const long long nctas = (long long)tiles_m2 * CM * p.tiles_n;
+    const long long nctas = (long long)tiles_m2 * CM * p.tiles_n * p.ksplit;
     if (nctas > 0x7fffffffll) return cudaErrorInvalidConfiguration;
     cudaLaunchConfig_t cfg{};
     cfg.gridDim = dim3((unsigned)nctas);
