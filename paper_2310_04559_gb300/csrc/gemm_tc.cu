@@ -32,8 +32,8 @@
 //            accumulation into caller data).  Single-level passes alternate the
 //            two accumulators so the MMAs of pass p+1 overlap the drain of pass p.
 //
-// Warp roles (192 threads): warp 0 TMA producer, warp 1 TMEM allocator + MMA
-// issuer (tcgen05.mma.cta_group::1, M=128, N=256), warps 2..5 epilogue
+// Warp roles (224 threads): warp 0 TMA producer, warps 1-2 MMA issuers
+// (tcgen05.mma.cta_group::1, M=128, N=256; warp 1 also allocates TMEM), warps 3..6 epilogue
 // (tcgen05.ld 32 lanes x 32 columns, transpose through shared memory, coalesced
 // global read-modify-write).  CTAs are rastered in groups of M-tiles so the
 // CTAs resident at once share their A and B tiles in L2.
@@ -62,7 +62,8 @@ static_assert((NA & (NA - 1)) == 0 && (NB & (NB - 1)) == 0, "ring sizes must be 
 constexpr int TILE_SMEM = NA * A_TILE + NB * B_TILE;  // 192 KB
 constexpr int MAX_SLICES = 8;
 constexpr int EPI_WARPS = 4;
-constexpr int THREADS = 64 + 32 * EPI_WARPS;
+constexpr int ISSUERS = 2;                     // MMA-issuing warps (one per level of a pair)
+constexpr int THREADS = 32 * (1 + ISSUERS + EPI_WARPS);
 constexpr int TMEM_COLS = 512;
 constexpr unsigned long long kDrainLimitNs = 1000000000ull;  // bound on the abort-path drains
 
@@ -70,7 +71,7 @@ struct SmemCtl {
     unsigned long long afull[NA], aempty[NA];
     unsigned long long bfull[NB], bempty[NB];
     unsigned long long tfull[2], tempty[2];
-    unsigned long long drain;
+    unsigned long long drain[ISSUERS];
     unsigned int tmem_base;
     volatile int abort;
     long long rowoff[BM];
@@ -346,10 +347,10 @@ gemm_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
     const uint16_t cmask = (uint16_t)((1u << CM) - 1);
 
     if (threadIdx.x == 0) {
-        for (int s = 0; s < NA; ++s) { mbar_init(&ctl->afull[s], 1); mbar_init(&ctl->aempty[s], 1); }
-        for (int s = 0; s < NB; ++s) { mbar_init(&ctl->bfull[s], 1); mbar_init(&ctl->bempty[s], CM); }
+        for (int s = 0; s < NA; ++s) { mbar_init(&ctl->afull[s], 1); mbar_init(&ctl->aempty[s], ISSUERS); }
+        for (int s = 0; s < NB; ++s) { mbar_init(&ctl->bfull[s], 1); mbar_init(&ctl->bempty[s], ISSUERS * CM); }
         for (int b = 0; b < 2; ++b) { mbar_init(&ctl->tfull[b], 1); mbar_init(&ctl->tempty[b], EPI_WARPS); }
-        mbar_init(&ctl->drain, 1);
+        for (int q = 0; q < ISSUERS; ++q) mbar_init(&ctl->drain[q], 1);
         ctl->abort = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
@@ -436,12 +437,18 @@ gemm_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
                 }
             }
         }
-    } else if (warp == 1) {
+    } else if (warp <= ISSUERS) {
         // ----------------------------------------------------------------- MMA
-        // Kept lean: the issue loop runs once per B tile (512-1024 cycles of MMA work),
-        // so per-tile bookkeeping uses registers only (no indexed local arrays), slot
-        // descriptors are precomputed and barrier tests take an inline fast path.
+        // Two issuing warps: issuing one tcgen05.mma costs the issuing thread about half
+        // of the MMA's own duration and the hardware queue is shallow, so a single issuer
+        // with per-tile barrier bookkeeping leaves the tensor pipe idle.  In a two-level
+        // pass issuer `me` owns level L1+me and its accumulator; both walk the same tile
+        // sequence, wait for the same tiles and release every slot (arrival count 2), so
+        // neither can run a phase ahead of the other.  In a one-level pass issuer 0 does
+        // all MMAs and issuer 1 only paces and releases.  Bookkeeping stays in registers;
+        // slot descriptors are slot 0's plus an offset; barrier tests take an inline fast path.
         if (lane == 0) {
+            const int me = warp - 1;
             const uint32_t idesc = instr_desc<KIND>();
             // slot q's descriptor = slot 0's + q * tile_bytes / 16 in the start-address field
             // (shared addresses stay below 256 KB, so the 14-bit field never carries over)
@@ -456,25 +463,23 @@ gemm_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
                 int lo, hi;
                 it.ranges(p, lo, hi);
                 const int L1 = p.glo[it.g], nl = p.gn[it.g], L2 = L1 + nl - 1;
-                // accumulator of level L1 (and L1+1 when the group has two levels)
-                const int buf0 = nl == 2 ? 0 : toggle;
-                const bool use0 = nl == 2 || buf0 == 0, use1 = nl == 2 || buf0 == 1;
+                const bool active = me < nl;
+                const int buf = nl == 2 ? me : toggle;
                 if (nl == 1) toggle ^= 1;
-                if (use0 && !mbar_try(&ctl->tempty[0], (tuse0 & 1) ^ 1) &&
-                    !mbar_wait(&ctl->tempty[0], (tuse0 & 1) ^ 1, ctl, p.status, p.wait_ns))
-                    ok = false;
-                if (ok && use1 && !mbar_try(&ctl->tempty[1], (tuse1 & 1) ^ 1) &&
-                    !mbar_wait(&ctl->tempty[1], (tuse1 & 1) ^ 1, ctl, p.status, p.wait_ns))
-                    ok = false;
+                const int mylevel = L1 + me;
+                if (active) {
+                    const uint32_t par = ((buf ? tuse1 : tuse0) & 1) ^ 1;
+                    if (!mbar_try(&ctl->tempty[buf], par) && !mbar_wait(&ctl->tempty[buf], par, ctl, p.status, p.wait_ns))
+                        ok = false;
+                }
                 if (!ok) break;
                 fence_after();
-                const uint32_t d0 = tmem + (uint32_t)(buf0 * BN), d1 = tmem + (uint32_t)BN;
-                uint32_t acc_bits = 0;  // bit lv: accumulator of level L1+lv already written this pass
+                const uint32_t d = tmem + (uint32_t)(buf * BN);
+                uint32_t acc = 0;
                 for (int kb = it.k0; kb < it.k1 && ok; kb += KSTEP) {
                     int a_wait = 0, a_free = 0;  // A tiles of this K-step waited for / released (i = hi - index)
                     for (int j = lo; j <= hi; ++j) {
                         const int imin = L1 - j > lo ? L1 - j : lo;
-                        const int imax = L2 - j < hi ? L2 - j : hi;
                         while (a_wait < hi - imin + 1) {
                             const uint32_t u = a_used + (uint32_t)a_wait;
                             unsigned long long* bar = &ctl->afull[u & (NA - 1)];
@@ -495,21 +500,23 @@ gemm_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
                                 break;
                             }
                         }
-                        const unsigned long long bd = bdesc0 + ((unsigned long long)bs << 11);
-                        for (int i = imax; i >= imin; --i) {
-                            const int lv = i + j - L1;
-                            const uint32_t d = lv ? d1 : d0;
-                            const unsigned long long ad =
-                                adesc0 + ((unsigned long long)((a_used + (uint32_t)(hi - i)) & (NA - 1)) << 10);
-                            const uint32_t acc = (acc_bits >> lv) & 1u;
-                            // four MMAs per 128-byte row: advance the start address by 32 bytes each
-                            mma<KIND>(d, ad, bd, idesc, acc);
-                            mma<KIND>(d, ad + 2, bd + 2, idesc, 1u);
-                            mma<KIND>(d, ad + 4, bd + 4, idesc, 1u);
-                            mma<KIND>(d, ad + 6, bd + 6, idesc, 1u);
-                            acc_bits |= 1u << lv;
+                        if (active) {
+                            const unsigned long long bd = bdesc0 + ((unsigned long long)bs << 11);
+                            // products of my level(s) with this B slice
+                            const int i_hi = (nl == 2 ? mylevel : L2) - j < hi ? (nl == 2 ? mylevel : L2) - j : hi;
+                            const int i_lo = (nl == 2 ? mylevel : L1) - j > lo ? (nl == 2 ? mylevel : L1) - j : lo;
+                            for (int i = i_hi; i >= i_lo; --i) {
+                                const unsigned long long ad =
+                                    adesc0 + ((unsigned long long)((a_used + (uint32_t)(hi - i)) & (NA - 1)) << 10);
+                                // four MMAs per 128-byte row: advance the start address by 32 bytes each
+                                mma<KIND>(d, ad, bd, idesc, acc);
+                                mma<KIND>(d, ad + 2, bd + 2, idesc, 1u);
+                                mma<KIND>(d, ad + 4, bd + 4, idesc, 1u);
+                                mma<KIND>(d, ad + 6, bd + 6, idesc, 1u);
+                                acc = 1;
+                                any = true;
+                            }
                         }
-                        any = true;
                         if (CM == 1) mma_commit(&ctl->bempty[bs]);
                         else mma_commit_mc(&ctl->bempty[bs], cmask);
                         ++b_used;
@@ -524,19 +531,21 @@ gemm_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
                     a_used += (uint32_t)(hi - lo + 1);
                 }
                 if (!ok) break;
-                if (use0) { mma_commit(&ctl->tfull[0]); ++tuse0; }
-                if (use1) { mma_commit(&ctl->tfull[1]); ++tuse1; }
+                if (active) {
+                    mma_commit(&ctl->tfull[buf]);
+                    if (buf) ++tuse1; else ++tuse0;
+                }
             } while (it.next(p));
             if (!ok && any) {
-                mma_commit(&ctl->drain);
-                mbar_drain_wait(&ctl->drain, 0, p.status);
+                mma_commit(&ctl->drain[me]);
+                mbar_drain_wait(&ctl->drain[me], 0, p.status);
             }
         }
     } else {
         // ------------------------------------------------------------ epilogue
         const int q4 = warp & 3;  // TMEM lane quarter this warp may access
         const int row0 = q4 * 32;
-        float(*stg)[33] = ctl->stage[warp - 2];
+        float(*stg)[33] = ctl->stage[warp - 1 - ISSUERS];
         uint32_t tuse0 = 0, tuse1 = 0;
         int toggle = 0;
         PassIter it;
