@@ -173,7 +173,8 @@ def run_ours(a):
     Lg, tg = L_h.to(dev), t2_h.to(dev)
     R = torch.empty_like(tg)
     E = torch.empty((), dtype=torch.float64, device=dev)
-    budget = int(a.budget_gb * (1 << 30))
+    # device-memory budget covers everything: inputs, R and the library's workspace
+    budget = int(a.budget_gb * 1e9) - L_np.nbytes - 2 * t2_np.nbytes - (2 << 30)
     ws_bytes = B.workspace_size(o, v, n, mode=mode, symmetric=True, budget=budget)
     ws = B.alloc_workspace(ws_bytes, dev)
     plan = B.plan(o, v, n, ws_bytes=ws_bytes, mode=mode, symmetric=True)
@@ -258,6 +259,7 @@ def run_ours(a):
            "config": {"workload": a.workload, "o": o, "v": v, "n_chol": n, "mode": mode, "order": plan["order"],
                       "a_block": plan["a_block"], "n_blocks": plan["n_blocks"], "pairs": plan["pairs"],
                       "symmetric_t": True, "workspace_gb": round(ws_bytes / 1e9, 2),
+                      "peak_device_gb": round(torch.cuda.max_memory_allocated(dev) / 1e9, 2),
                       "flops_algorithmic_per_step": flops, "flops_issued_per_step": plan["flops_issued"],
                       "l2": "inputs larger than L2 (L %.2f GB, t2 %.2f GB)" % (L_np.nbytes / 1e9, t2_np.nbytes / 1e9)},
            "e2e": e2e, "roofline": roofline, "clocks": clk.summary(), "gpu_launches": launches,
@@ -345,7 +347,7 @@ def main(argv=None):
     p.add_argument("--impl", choices=["ours", "reference"], default="ours")
     p.add_argument("--workload", choices=sorted(WORKLOADS), default="o40_v400_n2000")
     p.add_argument("--mode", default="ozaki_bf16")
-    p.add_argument("--budget-gb", type=float, default=150.0)
+    p.add_argument("--budget-gb", type=float, default=150.0, help="peak device memory (GB, 1e9 bytes)")
     p.add_argument("--e2e-steps", type=int, default=2)
     p.add_argument("--sample-a", type=int, default=1, help="oracle `a` columns for accuracy / CPU baseline")
     p.add_argument("--fp64-sample", type=int, default=20, help="`a` columns timed in plain FP64")

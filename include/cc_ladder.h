@@ -80,8 +80,12 @@ enum cc_order {
 /* Bit flags for cc_ladder_args.flags. */
 enum cc_flags {
     CC_FLAG_ACCUMULATE = 1,     /* R += term (the paper's `t_new += ...`, Section 3) instead of R = term */
-    CC_FLAG_SYMMETRIC_T = 2,    /* caller promises t2[i,j,c,d] == t2[j,i,d,c]; only pairs i <= j are
-                                   computed and R[j,i,b,a] = R[i,j,a,b] is written by symmetry        */
+    CC_FLAG_SYMMETRIC_T = 2,    /* caller promises t2[i,j,c,d] == t2[j,i,d,c], so R[j,i,b,a] = R[i,j,a,b].
+                                   Tensor-core modes, integral-first: the integrals are built for b >= a
+                                   only ((ac|bd) = (bd|ac) holds for any L) and the ladder GEMM runs on
+                                   the parts of t2 and (ac|bd) symmetric / antisymmetric in c <-> d,
+                                   packed over c <= d (about half the flops).  FP64 mode and the
+                                   Cholesky-first order compute the pairs i <= j and mirror them.    */
     CC_FLAG_EXCHANGE = 4,       /* evaluate the exchange partner of Eq. 7 instead:
                                    R[i,j,a,b] = sum_cd (sum_P L_Pad L_Pbc) t2[i,j,c,d]                */
     CC_FLAG_NO_STATUS_SYNC = 8  /* do not synchronise the stream at the end; device-side failures are
@@ -105,18 +109,21 @@ typedef struct cc_ladder_args {
     size_t budget_bytes;   /* workspace_size_ex only: upper bound for the plan (0 = 150 GB)     */
     void* stream;          /* cudaStream_t                                                      */
     int a_lo, a_hi;        /* range of virtual indices `a` to compute (both 0 = all of 0..v-1).
-                              Entries written: R[i,j,a,b] for a in [a_lo, a_hi); with
-                              CC_FLAG_SYMMETRIC_T, R[i,j,a,b] (i <= j) and R[j,i,b,a] (i < j) for
-                              a in the range.  Disjoint ranges write disjoint entries, so ranges
-                              spread over devices assemble R by a sum.  energy must be NULL
-                              unless the range is complete.                                      */
+                              Entries written: R[i,j,a,b] for a in [a_lo, a_hi).  With
+                              CC_FLAG_SYMMETRIC_T: in the tensor-core modes integral-first,
+                              R[i,j,a,b] and R[i,j,b,a] for all i, j, a in the range and b >= a;
+                              otherwise R[i,j,a,b] (i <= j) and R[j,i,b,a] (i < j) for a in the
+                              range.  Either way disjoint ranges write disjoint entries, so ranges
+                              spread over devices (each R zeroed first) assemble R by a sum.
+                              energy must be NULL unless the range is complete.                  */
 } cc_ladder_args;
 
 /* What the planner decided for a call (for reporting and tests). */
 typedef struct cc_ladder_plan {
     int order;             /* CC_ORDER_INTEGRAL_FIRST or CC_ORDER_CHOLESKY_FIRST */
-    int a_block;           /* `a` values per block                               */
-    int n_blocks;          /* ceil(v / a_block)                                  */
+    int a_block;           /* `a` values in the first block                      */
+    int n_blocks;          /* number of blocks (pair-symmetric tensor-core plans widen their
+                              blocks as the b >= a range shrinks)                 */
     int slices;            /* Ozaki slices (1 for the non-emulated modes)        */
     int pairs;             /* GEMM rows used for (i,j): o*o, or o(o+1)/2 with symmetry */
     size_t ws_bytes;       /* workspace the plan needs                           */

@@ -10,8 +10,18 @@
 // Forward, Cholesky-first order (Section 3.2, the L.t intermediate):
 //     CF1  X[ij,a,P,d] = sum_c L[P,a,c] t2[ij,c,d]            (GEMM M=A*n, N=o^2*v, K=v)
 //     CF2  R[ij,a,b]   = sum_(P,d) X[ij,a,P,d] L[P,b,d]        (GEMM M=o^2*A, N=v, K=n*v)
+// Pair-symmetric amplitudes (CC_FLAG_SYMMETRIC_T), integral-first, tensor-core modes
+// ("packed" path, pm.cu): since (ac|bd) = (bd|ac) for any L, a block only needs the
+// integrals with b >= a (KG1 skips the tiles below that diagonal), and the ladder
+// GEMM is done on the parts of t2 and of the integrals symmetric and antisymmetric
+// under c <-> d, packed over c <= d:
+//     KG1   V[al][b'][c][d], b = a0 + b' >= a                   (GEMM M=A*v, N=(v-a0)*v, K=n)
+//     R+[i<=j][(a,b>=a)] = sum_{c<=d} T+[ij][cd] V+[ab][cd]      (GEMM M=o(o+1)/2, K=v(v+1)/2)
+//     R-[i< j][(a,b>=a)] = sum_{c< d} T-[ij][cd] V-[ab][cd]      (GEMM M=o(o-1)/2, K=v(v-1)/2)
+//     R[i,j,a,b] = R[j,i,b,a] = R+ + R-,  R[j,i,a,b] = R[i,j,b,a] = R+ - R-
+// which issues about (n + o^2/2) v^4 multiply-adds instead of 2 (n + o(o+1)/2) v^4.
 // In the emulated-FP64 and mixed modes every GEMM operand is first turned into
-// a slice stack (split.cu) and the GEMM runs on the tensor cores (gemm_tc.cu);
+// a slice stack (split.cu, pm.cu) and the GEMM runs on the tensor cores (gemm_tc.cu);
 // in the FP64 mode the GEMMs run on DMMA (gemm_f64.cu) straight from FP64.
 #include <cuda_runtime.h>
 
@@ -21,6 +31,8 @@
 #include <cstdlib>
 #include <map>
 #include <tuple>
+#include <utility>
+#include <vector>
 #include <cmath>
 #include <cstdint>
 #include <cstring>
@@ -63,11 +75,33 @@ struct Ctx {
     int mode, order, flags, s;
     bool sym, exch;
     long long pairs;  // GEMM rows for (i,j)
+    bool packed;      // pair-symmetric integral-first tensor-core path (R+ / R- over c <= d)
+    long long pp, pm; // packed path: pairs i <= j and i < j
+    long long Kp, Km; // packed path: v(v+1)/2 and v(v-1)/2
 };
+
+// Blocks of `a` values [a0, a0 + Ab) covering [alo, ahi).  Unpacked paths: Ab = P
+// for every block.  Packed path: a block holds the integrals (a, b >= a0), so its
+// size is Ab * (v - a0) rows; P bounds that product and blocks widen as a0 grows.
+std::vector<std::pair<int, int>> block_list(const Ctx& c, long long P, int alo, int ahi, int forced)
+{
+    std::vector<std::pair<int, int>> out;
+    for (int a0 = alo; a0 < ahi;) {
+        int Ab;
+        if (!c.packed) Ab = (int)std::min<long long>(P, ahi - a0);
+        else if (forced > 0) Ab = std::min(forced, ahi - a0);
+        else Ab = (int)std::max(1ll, std::min<long long>(P / (c.v - a0), ahi - a0));
+        out.emplace_back(a0, Ab);
+        a0 += Ab;
+    }
+    return out;
+}
 
 // ------------------------------------------------------------------ workspace
 struct FwdLayout {
     size_t status, pairtab, t2x, Rc, epart, epair;
+    // packed path
+    size_t pairtab_m, rtab, Tp, eTp, Tm, eTm, Vp, eVp, Vm, eVm, Rpc, Rmc;
     // integral-first
     size_t V, Lw, eL, colmax, tw, et, Vw, eV;
     // Cholesky-first
@@ -75,8 +109,42 @@ struct FwdLayout {
     size_t total;
 };
 
-FwdLayout layout_fwd(const Ctx& c, int A)
+// Packed path: P = capacity in integral rows (a, b), P >= max over blocks of Ab * (v - a0).
+FwdLayout layout_packed(const Ctx& c, long long P)
 {
+    FwdLayout L{};
+    Carve cv;
+    const long long o = c.o, v = c.v, n = c.n, vv = v * v;
+    const int es = esz_of(c.mode);
+    const long long s = c.s;
+    L.status = cv.take(256);
+    L.pairtab = cv.take(8 * c.pp);
+    L.pairtab_m = cv.take(8 * std::max(1ll, c.pm));
+    if (c.exch) L.t2x = cv.take(8 * o * o * vv);
+    L.epart = cv.take(8 * energy_scratch_doubles(c.o, c.v));
+    L.epair = cv.take(8 * o * o);
+    L.V = cv.take(8 * P * vv);
+    L.Lw = cv.take(es * s * vv * pitch_for(n, es));
+    L.eL = cv.take(4 * vv);
+    L.colmax = cv.take(8 * vv);
+    L.Tp = cv.take(es * s * c.pp * pitch_for(c.Kp, es));
+    L.eTp = cv.take(4 * c.pp);
+    L.Tm = cv.take(es * s * c.pm * pitch_for(c.Km, es));
+    L.eTm = cv.take(4 * c.pm);
+    L.rtab = cv.take(8 * P);
+    L.Vp = cv.take(es * s * P * pitch_for(c.Kp, es));
+    L.eVp = cv.take(4 * P);
+    L.Vm = cv.take(es * s * P * pitch_for(c.Km, es));
+    L.eVm = cv.take(4 * P);
+    L.Rpc = cv.take(8 * c.pp * P);
+    L.Rmc = cv.take(8 * c.pm * P);
+    L.total = cv.cur;
+    return L;
+}
+
+FwdLayout layout_fwd(const Ctx& c, long long A)
+{
+    if (c.packed) return layout_packed(c, A);
     FwdLayout L{};
     Carve cv;
     const long long o = c.o, v = c.v, n = c.n, vv = v * v, P = c.pairs;
@@ -124,7 +192,12 @@ struct BwdLayout {
 };
 
 // ------------------------------------------------------------------ planner
-double flops_if(const Ctx& c) { return 2.0 * ((double)c.pairs + c.n) * std::pow((double)c.v, 4); }
+double flops_if(const Ctx& c)
+{
+    if (c.packed)
+        return std::pow((double)c.v, 2) * (c.n * (double)c.v * (c.v + 1) + 2.0 * ((double)c.pp * c.Kp + (double)c.pm * c.Km));
+    return 2.0 * ((double)c.pairs + c.n) * std::pow((double)c.v, 4);
+}
 double flops_cf(const Ctx& c) { return 4.0 * c.n * (double)c.pairs * std::pow((double)c.v, 3); }
 
 // ---------------------------------------------------------------- autotuner
@@ -190,24 +263,30 @@ int pick_order(const Ctx& c, int requested)
     return cf < itf ? CC_ORDER_CHOLESKY_FIRST : CC_ORDER_INTEGRAL_FIRST;
 }
 
-// Largest block fitting `bytes`, then evened out over the blocks it implies.
-int pick_block(const Ctx& c, size_t bytes, int requested, size_t* need)
+// Layout parameter fitting `bytes`: the block size A (unpacked paths: largest A, then
+// evened out over the blocks it implies), or the integral-row capacity P (packed path:
+// largest P in [v, v^2]; a requested a_block A means P = A v).  -1 if nothing fits.
+long long pick_block(const Ctx& c, size_t bytes, int requested, size_t* need)
 {
+    const long long unit = c.packed ? c.v : 1;
     if (requested > 0) {
-        const int A = std::min(requested, c.v);
-        *need = layout_fwd(c, A).total;
-        return *need <= bytes ? A : -1;
+        const long long P = (long long)std::min(requested, c.v) * unit;
+        *need = layout_fwd(c, P).total;
+        return *need <= bytes ? P : -1;
     }
-    if (layout_fwd(c, 1).total > bytes) { *need = layout_fwd(c, 1).total; return -1; }
-    int lo = 1, hi = c.v;
+    if (layout_fwd(c, unit).total > bytes) { *need = layout_fwd(c, unit).total; return -1; }
+    long long lo = unit, hi = (long long)c.v * unit;
     while (lo < hi) {
-        const int mid = (lo + hi + 1) / 2;
+        const long long mid = (lo + hi + 1) / 2;
         if (layout_fwd(c, mid).total <= bytes) lo = mid; else hi = mid - 1;
     }
-    const int nb = (c.v + lo - 1) / lo;
-    const int A = (c.v + nb - 1) / nb;
-    *need = layout_fwd(c, A).total;
-    return A;
+    long long P = lo;
+    if (!c.packed) {
+        const long long nb = (c.v + lo - 1) / lo;
+        P = (c.v + nb - 1) / nb;
+    }
+    *need = layout_fwd(c, P).total;
+    return P;
 }
 
 int make_ctx(const cc_ladder_args* a, Ctx* c)
@@ -230,7 +309,16 @@ int make_ctx(const cc_ladder_args* a, Ctx* c)
     c->sym = (a->flags & CC_FLAG_SYMMETRIC_T) != 0;
     c->exch = (a->flags & CC_FLAG_EXCHANGE) != 0;
     c->pairs = c->sym ? (long long)a->o * (a->o + 1) / 2 : (long long)a->o * a->o;
+    c->pp = (long long)a->o * (a->o + 1) / 2;
+    c->pm = (long long)a->o * (a->o - 1) / 2;
+    c->Kp = (long long)a->v * (a->v + 1) / 2;
+    c->Km = (long long)a->v * (a->v - 1) / 2;
+    // the packed path needs the pair symmetry and runs the tensor-core modes integral-first;
+    // the order's cost model sees the packed flop count
+    const bool can_pack = c->sym && is_tc(a->mode);
+    c->packed = can_pack;
     c->order = pick_order(*c, a->order);
+    c->packed = can_pack && c->order == CC_ORDER_INTEGRAL_FIRST;
     return CC_OK;
 }
 
@@ -298,12 +386,31 @@ int prep_cols(const Ctx& c, const ColSrc& src, Operand& op, unsigned long long* 
 
 double tc_products(const Ctx& c) { return c.mode == CC_OZAKI_BF16 ? c.s * (c.s + 1) / 2.0 : 1.0; }
 
+// Output elements of an M x N slice GEMM that lie in tiles the triangular skip keeps
+// (a(m) = m / tri, b(n) = n / tri; a tile goes when b < a for all its elements).
+// Tile edges as in gemm_tc.cu (128 x 256).
+double tri_elems(long long M, long long N, long long tri)
+{
+    if (tri <= 0) return (double)M * N;
+    constexpr long long TM = 128, TN = 256;
+    double e = 0.0;
+    for (long long m0 = 0; m0 < M; m0 += TM) {
+        const long long need = (m0 / tri) * tri;  // smallest n whose b reaches a(m0)
+        if (need > N - 1) continue;
+        const long long t0 = need >= TN - 1 ? (need - TN + 1 + TN - 1) / TN : 0;
+        e += (double)std::min(TM, M - m0) * (double)(N - t0 * TN);
+    }
+    return e;
+}
+
 // intermediate: the output feeds another slice GEMM through split_fixed_rows, so in
 // the emulated mode it stays int64 fixed point (no FP64 work, no loads in the epilogue).
+// tri > 0: triangular tile skip with a(m) = m / tri, b(n) = n / tri.
 int run_tc(const char* name, const Ctx& c, int M, int N, int K, const Operand& A, long long rowA0, const Operand& B,
-           long long rowB0, const OutDesc& out, int* status, cudaStream_t st, bool intermediate = false)
+           long long rowB0, const OutDesc& out, int* status, cudaStream_t st, bool intermediate = false,
+           long long tri = 0)
 {
-    ProfScope ps(name, st, 2.0 * M * (double)N * K * tc_products(c));
+    ProfScope ps(name, st, 2.0 * tri_elems(M, N, tri) * K * tc_products(c));
     GemmTc g{};
     g.kind = c.mode == CC_TF32 ? TC_TF32 : TC_BF16;
     g.M = M; g.N = N; g.K = K;
@@ -348,6 +455,7 @@ int run_tc(const char* name, const Ctx& c, int M, int N, int K, const Operand& A
         g.epi = EPI_FP64_RMW;
         g.fixF = 0;
     }
+    g.tri_rdiv = g.tri_cdiv = tri;
     g.out = out;
     g.status = status;
     g.wait_ns = g_wait_ns.load();
@@ -363,6 +471,75 @@ template <typename T>
 T* at(void* ws, size_t off) { return (T*)((char*)ws + off); }
 
 // ----------------------------------------------------------------- forward
+// Packed path (pair-symmetric t2, integral-first, tensor-core modes): see the header
+// comment.  R receives R[i,j,a,b] and R[i,j,b,a] for all i, j, a in [alo, ahi), b >= a.
+int fwd_packed(const Ctx& c, const cc_ladder_args* a, const double* Lsrc, const double* t2, long long P,
+               const FwdLayout& Lo, void* ws, int* status, cudaStream_t st, int alo, int ahi)
+{
+    const long long v = c.v, n = c.n, vv = v * v;
+    const bool ozaki = c.mode == CC_OZAKI_BF16;
+    const int kind = ozaki ? 0 : (c.mode == CC_BF16 ? 1 : 2);
+    const int es = esz_of(c.mode);
+    long long* pairtab = at<long long>(ws, Lo.pairtab);
+    long long* pairtab_m = at<long long>(ws, Lo.pairtab_m);
+    long long* rtab = at<long long>(ws, Lo.rtab);
+    CC_CU(fill_pairs(c.o, c.v, 0, pairtab, st));
+    CC_CU(fill_pairs(c.o, c.v, 1, pairtab_m, st));
+    const bool minus = c.pm > 0 && c.Km > 0;
+
+    Operand Lw{}, Tp{}, Tm{}, Vp{}, Vm{};
+    Lw.D = at<void>(ws, Lo.Lw); Lw.e = at<int>(ws, Lo.eL);
+    Tp.D = at<void>(ws, Lo.Tp); Tp.e = at<int>(ws, Lo.eTp); Tp.rows = c.pp; Tp.pitch = pitch_for(c.Kp, es);
+    Tm.D = at<void>(ws, Lo.Tm); Tm.e = at<int>(ws, Lo.eTm); Tm.rows = c.pm; Tm.pitch = pitch_for(c.Km, es);
+    Vp.D = at<void>(ws, Lo.Vp); Vp.e = at<int>(ws, Lo.eVp); Vp.pitch = Tp.pitch;
+    Vm.D = at<void>(ws, Lo.Vm); Vm.e = at<int>(ws, Lo.eVm); Vm.pitch = Tm.pitch;
+    {
+        // L rows (a,c) are contiguous in L[P][a][c]; K = P is strided
+        ColSrc ls{Lsrc, vv, vv, n, 0, plain_map(0)};
+        CC_TRY(prep_cols(c, ls, Lw, at<unsigned long long>(ws, Lo.colmax), st));
+        ProfScope ps("split", st);
+        CC_CU(pm_split_f64(t2, pairtab, 1, c.pp, c.v, +1, 1.0, kind, c.s, kBeta, Tp.D, Tp.pitch, Tp.e, st));
+        if (minus)
+            CC_CU(pm_split_f64(t2, pairtab_m, 1, c.pm, c.v, -1, 1.0, kind, c.s, kBeta, Tm.D, Tm.pitch, Tm.e, st));
+    }
+    double* V = at<double>(ws, Lo.V);
+    double* Rpc = at<double>(ws, Lo.Rpc);
+    double* Rmc = at<double>(ws, Lo.Rmc);
+    const int accum = (c.flags & CC_FLAG_ACCUMULATE) ? 1 : 0;
+    for (const auto& blk : block_list(c, P, alo, ahi, a->a_block)) {
+        const int a0 = blk.first, Ab = blk.second, Nb = c.v - a0;
+        const long long nr = (long long)Ab * Nb - (long long)Ab * (Ab - 1) / 2;
+        // KG1: V[al][b'][c][d] = sum_P L[P, a0+al, c] L[P, a0+b', d], tiles with b < a skipped
+        OutDesc o1{V, split_map(v, (long long)Nb * vv, v), split_map(v, vv, 1), 0};
+        CC_TRY(run_tc("kg1_tc", c, Ab * c.v, Nb * c.v, c.n, Lw, (long long)a0 * v, Lw, (long long)a0 * v, o1, status,
+                      st, true, v));
+        CC_CU(fill_rtab(Ab, Nb, rtab, st));
+        Vp.rows = nr; Vm.rows = nr;
+        {
+            ProfScope ps("split", st);
+            if (ozaki) {
+                // V[al][b'][c][d] = X * 2^(eL[(a0+al)v + c] + eL[(a0+b')v + d] + base)
+                PmFixedSrc fs{(const long long*)V, rtab, nr, vv, c.v, Lw.e, split_map(Nb, v, 0, (long long)a0 * v),
+                              Lw.e, split_map(Nb, 0, v, (long long)a0 * v), kFixedBase};
+                CC_CU(pm_split_fixed(fs, c.s, kBeta, Vp.D, Vp.pitch, Vp.e, minus ? Vm.D : nullptr, Vm.pitch, Vm.e, st));
+            } else {
+                CC_CU(pm_split_f64(V, rtab, vv, nr, c.v, +1, 0.5, kind, c.s, kBeta, Vp.D, Vp.pitch, Vp.e, st));
+                if (minus)
+                    CC_CU(pm_split_f64(V, rtab, vv, nr, c.v, -1, 0.5, kind, c.s, kBeta, Vm.D, Vm.pitch, Vm.e, st));
+            }
+        }
+        OutDesc op{Rpc, plain_map(nr), plain_map(1), 0};
+        CC_TRY(run_tc("kg2_tc", c, (int)c.pp, (int)nr, (int)c.Kp, Tp, 0, Vp, 0, op, status, st));
+        if (minus) {
+            OutDesc om{Rmc, plain_map(nr), plain_map(1), 0};
+            CC_TRY(run_tc("kg2_tc", c, (int)c.pm, (int)nr, (int)c.Km, Tm, 0, Vm, 0, om, status, st));
+        }
+        ProfScope ps("scatter", st);
+        CC_CU(pm_combine(c.o, c.v, a0, Ab, Nb, nr, Rpc, minus ? Rmc : nullptr, a->R, accum, st));
+    }
+    return CC_OK;
+}
+
 int fwd_impl(const cc_ladder_args* a, const double* Lsrc_override = nullptr)
 {
     Ctx c;
@@ -374,9 +551,10 @@ int fwd_impl(const cc_ladder_args* a, const double* Lsrc_override = nullptr)
         return CC_ERR_ALIGN;
     if (is_tc(c.mode) && !tc_gemm_available()) return CC_ERR_UNSUPPORTED;
     size_t need = 0;
-    const int A = pick_block(c, a->ws_bytes, a->a_block, &need);
-    if (A < 0) return CC_ERR_WORKSPACE;
-    const FwdLayout Lo = layout_fwd(c, A);
+    const long long Pblk = pick_block(c, a->ws_bytes, a->a_block, &need);
+    if (Pblk < 0) return CC_ERR_WORKSPACE;
+    const FwdLayout Lo = layout_fwd(c, Pblk);
+    const int A = (int)Pblk;
     void* ws = a->workspace;
     cudaStream_t st = (cudaStream_t)a->stream;
     const long long o = c.o, v = c.v, n = c.n, vv = v * v;
@@ -389,6 +567,15 @@ int fwd_impl(const cc_ladder_args* a, const double* Lsrc_override = nullptr)
     if (c.exch) {  // Eq. 7 = Eq. 6 applied to t2 with c <-> d swapped
         CC_CU(swap_last2(o * o, c.v, a->t2, at<double>(ws, Lo.t2x), st));
         t2 = at<double>(ws, Lo.t2x);
+    }
+    if (c.packed) {
+        CC_TRY(fwd_packed(c, a, Lsrc, t2, Pblk, Lo, ws, status, st, alo, ahi));
+        if (a->energy) {
+            ProfScope ps("energy", st);
+            CC_CU(energy_pairs(c.o, c.v, a->R, a->t2, at<double>(ws, Lo.epart), at<double>(ws, Lo.epair), st));
+            CC_CU(energy_total(c.o * c.o, at<double>(ws, Lo.epair), a->energy, st));
+        }
+        return finish(status, c.flags, st);
     }
     long long* pairtab = c.sym ? at<long long>(ws, Lo.pairtab) : nullptr;
     if (c.sym) CC_CU(fill_pair_table(c.o, c.v, pairtab, st));
@@ -737,8 +924,7 @@ int cc_ladder_workspace_size_ex(const cc_ladder_args* args, size_t* bytes)
     CC_TRY(make_ctx(args, &c));
     const size_t budget = args->budget_bytes ? args->budget_bytes : kDefaultBudget;
     size_t need = 0;
-    const int A = pick_block(c, budget, args->a_block, &need);
-    if (A < 0) return args->a_block > 0 ? CC_ERR_BUDGET : CC_ERR_BUDGET;
+    if (pick_block(c, budget, args->a_block, &need) < 0) return CC_ERR_BUDGET;
     *bytes = need;
     return CC_OK;
 }
@@ -757,21 +943,32 @@ int cc_ladder_plan_query(const cc_ladder_args* args, cc_ladder_plan* plan)
     CC_TRY(make_ctx(args, &c));
     size_t need = 0;
     const size_t bytes = args->ws_bytes ? args->ws_bytes : (args->budget_bytes ? args->budget_bytes : kDefaultBudget);
-    const int A = pick_block(c, bytes, args->a_block, &need);
-    if (A < 0) return CC_ERR_WORKSPACE;
+    const long long P = pick_block(c, bytes, args->a_block, &need);
+    if (P < 0) return CC_ERR_WORKSPACE;
+    const int alo = args->a_hi ? args->a_lo : 0, ahi = args->a_hi ? args->a_hi : c.v;
+    const auto blocks = block_list(c, P, alo, ahi, args->a_block);
     plan->order = c.order;
-    plan->a_block = A;
-    plan->n_blocks = (c.v + A - 1) / A;
+    plan->a_block = blocks.empty() ? 0 : blocks[0].second;
+    plan->n_blocks = (int)blocks.size();
     plan->slices = c.s;
     plan->pairs = (int)c.pairs;
     plan->ws_bytes = need;
-    const double v = c.v, o2 = (double)c.o * c.o;
-    plan->flops_algorithmic = c.order == CC_ORDER_INTEGRAL_FIRST ? 2.0 * (o2 + c.n) * v * v * v * v
-                                                                 : 4.0 * c.n * o2 * v * v * v;
-    const double nprod = c.mode == CC_OZAKI_BF16 ? c.s * (c.s + 1) / 2.0 : 1.0;
-    const double base = c.order == CC_ORDER_INTEGRAL_FIRST ? 2.0 * ((double)c.pairs + c.n) * v * v * v * v
-                                                           : 4.0 * c.n * (double)c.pairs * v * v * v;
-    plan->flops_issued = base * nprod;
+    const double v = c.v, o2 = (double)c.o * c.o, frac = (double)(ahi - alo) / c.v;
+    plan->flops_algorithmic = (c.order == CC_ORDER_INTEGRAL_FIRST ? 2.0 * (o2 + c.n) * v * v * v * v
+                                                                  : 4.0 * c.n * o2 * v * v * v) * frac;
+    const double nprod = tc_products(c);
+    double issued = 0.0;
+    if (c.packed) {
+        for (const auto& b : blocks) {
+            const long long Ab = b.second, Nb = c.v - b.first;
+            const double nr = (double)Ab * Nb - (double)Ab * (Ab - 1) / 2;
+            issued += 2.0 * c.n * tri_elems(Ab * c.v, Nb * c.v, c.v) + 2.0 * nr * ((double)c.pp * c.Kp + (double)c.pm * c.Km);
+        }
+    } else {
+        issued = (c.order == CC_ORDER_INTEGRAL_FIRST ? 2.0 * ((double)c.pairs + c.n) * v * v * v * v
+                                                     : 4.0 * c.n * (double)c.pairs * v * v * v) * frac;
+    }
+    plan->flops_issued = issued * nprod;
     return CC_OK;
 }
 
@@ -796,15 +993,17 @@ int cc_ladder_autotune(const cc_ladder_args* args, cc_ladder_plan* plan, double*
         Ctx cq;
         make_ctx(&a, &cq);
         size_t need = 0;
-        const int A = pick_block(cq, a.ws_bytes, a.a_block, &need);
-        if (A < 0) continue;  // this order does not fit the workspace
+        const long long P = pick_block(cq, a.ws_bytes, a.a_block, &need);
+        if (P < 0) continue;  // this order does not fit the workspace
         // time one block and (when there is one) two blocks: fixed cost + per-block cost
+        // (packed blocks are sized to about equal work, so the extrapolation holds there too)
         double t[2] = {0.0, 0.0};
-        const int nb = (c.v + A - 1) / A;
+        const auto blocks = block_list(cq, P, 0, c.v, a.a_block);
+        const int nb = (int)blocks.size();
         const int reps = nb >= 2 ? 2 : 1;
         for (int r = 0; r < reps && status == CC_OK; ++r) {
             a.a_lo = 0;
-            a.a_hi = std::min(c.v, (r + 1) * A);
+            a.a_hi = blocks[r].first + blocks[r].second;
             status = fwd_impl(&a);  // warm (first use of the shape)
             if (status != CC_OK) break;
             cudaEventRecord(e0, st);

@@ -82,6 +82,9 @@ struct GemmTc {
     int gkc[kMaxGroups];        // K elements per pass (0 = whole K; else a multiple of 64 bf16 / 32 tf32)
     int epi, fixF;              // TcEpi; fixed-point fraction bits for EPI_FIXED64
     int ksplit;                 // K split across this many CTAs per tile (EPI_FIXED64_ADD only; 1 = none)
+    // Triangular tile skip (0 = off): with a(m) = m / tri_rdiv and b(n) = n / tri_cdiv, a CTA
+    // whose tile has b(n) < a(m) for every element writes nothing (integral blocks with b >= a).
+    long long tri_rdiv, tri_cdiv;
     OutDesc out;
     int* status;                // device status word (bit 0: wait bound expired)
     unsigned long long wait_ns; // bound on every device-side wait
@@ -124,6 +127,33 @@ struct FixedSrc {
 };
 cudaError_t split_fixed_rows_bf16(const FixedSrc& src, int s, int beta, void* D, long long pitch, int* e,
                                   cudaStream_t st);
+// Symmetric / antisymmetric packing (pm.cu) for pair-symmetric amplitudes.
+// Packed rows of an FP64 source: row r is the v x v matrix at X + (rowtab ? rowtab[r] : r) * rowmul;
+// sign > 0 writes the c <= d part (X[c][d] + X[d][c]) * h (diagonal X[c][c]) at c*v - c(c-1)/2 + d - c,
+// sign < 0 the c < d part (X[c][d] - X[d][c]) * h at c*(v-1) - c(c-1)/2 + d - c - 1.  kind 0: Ozaki
+// digits with a row exponent, 1: bf16 copy (e = 0), 2: tf32 copy (e may be NULL).
+cudaError_t pm_split_f64(const double* X, const long long* rowtab, long long rowmul, long long rows, int v, int sign,
+                         double h, int kind, int s, int beta, void* D, long long pitch, int* e, cudaStream_t st);
+// Int64 fixed-point integral block: packed row r is unpacked row ru = rtab[r] of X (ldx per row),
+// X[c][d] * 2^(eA[amap(ru) + c] + eB[bmap(ru) + d] + base).  Writes V+ (h = 1/2) and, if Dm is not
+// NULL, V- digits, both with the row exponent of max |V|.
+struct PmFixedSrc {
+    const long long* X; const long long* rtab; long long rows, ldx;
+    int v;
+    const int* eA; Map2 amap;
+    const int* eB; Map2 bmap;
+    int base;
+};
+cudaError_t pm_split_fixed(const PmFixedSrc& src, int s, int beta, void* Dp, long long pitchp, int* ep, void* Dm,
+                           long long pitchm, int* em, cudaStream_t st);
+// rtab[rowbase(al) + b' - al] = al * Nb + b' for al < Ab, al <= b' < Nb (rowbase(al) = al Nb - al(al-1)/2)
+cudaError_t fill_rtab(int Ab, int Nb, long long* rtab, cudaStream_t st);
+// R[i,j,a,b], R[j,i,b,a] (=|+=) R+ + R-;  R[j,i,a,b], R[i,j,b,a] (=|+=) R+ - R-  for the block
+// a = a0 + al (al < Ab), b = a0 + b' (al <= b' < Nb); Rp[p][r] over pairs i <= j, Rm[q][r] over i < j.
+cudaError_t pm_combine(int o, int v, int a0, int Ab, int Nb, long long nr, const double* Rp, const double* Rm, double* R,
+                       int accumulate, cudaStream_t st);
+// tab = (i*o + j) * v*v for the pairs i < j (strict = 1) or i <= j (strict = 0), i-major
+cudaError_t fill_pairs(int o, int v, int strict, long long* tab, cudaStream_t st);
 // Plain fp64 -> tf32 (stored as fp32) copies, K-major.
 cudaError_t convert_rows_tf32(const RowSrc& src, float* D, long long pitch, cudaStream_t st);
 cudaError_t convert_cols_tf32(const ColSrc& src, float* D, long long pitch, cudaStream_t st);

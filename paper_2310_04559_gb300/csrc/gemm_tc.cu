@@ -90,6 +90,7 @@ struct Params {
     int glo[kMaxGroups], gn[kMaxGroups], gkc[kMaxGroups];
     int epi, fixF;
     int ksplit, kper;            // K split: CTA split s owns [s*kper, min(K, (s+1)*kper))
+    long long tri_rdiv, tri_cdiv;  // triangular tile skip (0 = off)
     int tiles_m, tiles_n, group_m;
     OutDesc out;
     int* status;
@@ -345,6 +346,12 @@ gemm_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
     const int m0 = ((first_m + (t % per_group) % gm) * CM + rank) * BM;
     const int n0 = ((t % per_group) / gm) * BN;
     const uint16_t cmask = (uint16_t)((1u << CM) - 1);
+    // triangular skip (the host launches CM == 1 with it): every element of the tile has
+    // b(n) < a(m), so nothing of it is needed; leave before any barrier or TMEM is touched
+    if (p.tri_rdiv > 0) {
+        const long long nmax = min((long long)p.N - 1, (long long)n0 + BN - 1);
+        if (nmax / p.tri_cdiv < (long long)m0 / p.tri_rdiv) return;
+    }
 
     if (threadIdx.x == 0) {
         for (int s = 0; s < NA; ++s) { mbar_init(&ctl->afull[s], 1); mbar_init(&ctl->aempty[s], ISSUERS); }
@@ -767,6 +774,9 @@ cudaError_t gemm_tc(const GemmTc& g, cudaStream_t s)
     p.kper = (int)((((long long)g.K + p.ksplit - 1) / p.ksplit + kstep - 1) / kstep * kstep);
     for (int i = 0; i < g.ngroups; ++i)
         if (p.ksplit > 1 && g.gkc[i] != 0) return cudaErrorInvalidValue;
+    if ((g.tri_rdiv > 0) != (g.tri_cdiv > 0) || g.tri_rdiv < 0) return cudaErrorInvalidValue;
+    p.tri_rdiv = g.tri_rdiv;
+    p.tri_cdiv = g.tri_cdiv;
     p.out = g.out;
     p.status = g.status;
     p.wait_ns = g.wait_ns;
@@ -779,7 +789,7 @@ cudaError_t gemm_tc(const GemmTc& g, cudaStream_t s)
         const char* e = getenv("CC_LADDER_TC_CLUSTER");
         return (e && e[0] == '2') ? 2 : 1;
     }();
-    const int CM = (p.tiles_m >= 2 && cluster_pref == 2) ? 2 : 1;
+    const int CM = (p.tiles_m >= 2 && cluster_pref == 2 && p.tri_rdiv == 0) ? 2 : 1;
     const int tiles_m2 = (p.tiles_m + CM - 1) / CM;
     p.group_m = tiles_m2 < 8 ? tiles_m2 : 8;
     CUtensorMap ma, mb;

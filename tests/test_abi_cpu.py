@@ -101,8 +101,16 @@ def test_workspace_queries_monotone_in_budget(lib):
     # the plan the forward would run for exactly the queried bytes is the same block
     ws = Ld.workspace_size(40, 400, 2000, mode="ozaki_bf16", symmetric=True, budget=40 << 30)
     p = Ld.plan(40, 400, 2000, ws_bytes=ws, mode="ozaki_bf16", symmetric=True)
-    assert p["ws_bytes"] == ws and p["n_blocks"] * p["a_block"] >= 400
+    # pair-symmetric tensor-core plans widen their blocks as the b >= a range shrinks
+    assert p["ws_bytes"] == ws and 1 <= p["n_blocks"] <= -(-400 // p["a_block"])
     assert p["flops_algorithmic"] == 2.0 * (1600 + 2000) * 400 ** 4
+    # ... and issue about (n + o^2/2) v^4 multiply-adds per slice product instead of 2 (n + o(o+1)/2) v^4
+    unpacked = 21 * 2.0 * (820 + 2000) * 400 ** 4
+    assert 0.45 < p["flops_issued"] / unpacked < 0.6
+    # FP64 (DMMA) plans keep uniform blocks
+    ws = Ld.workspace_size(40, 400, 2000, mode="fp64", symmetric=True, budget=40 << 30)
+    p = Ld.plan(40, 400, 2000, ws_bytes=ws, mode="fp64", symmetric=True)
+    assert p["ws_bytes"] == ws and p["n_blocks"] * p["a_block"] >= 400
 
 
 def test_planner_orders(lib):

@@ -93,6 +93,37 @@ def test_ragged_multiblock(dev, oracle, mode):
             assert rel(R, R_ref) < TOL[mode], (order, ab, rel(R, R_ref))
 
 
+@pytest.mark.parametrize("mode", MODES)
+@pytest.mark.parametrize("a_block", [0, 7, 1])
+def test_pair_symmetric_ragged_blocks(dev, oracle, mode, a_block):
+    """Pair-symmetric t2 with a non-symmetric L (the kernels may use (ac|bd) = (bd|ac),
+    never L_Pac = L_Pca): ragged tiles, forced small a-blocks and one `a` per block, so
+    the b >= a integral blocks, the c <= d packing and the four-way write of R meet
+    every diagonal case."""
+    o, v, n = 5, 37, 150
+    rng = np.random.default_rng(31)
+    L = synth.cholesky_vectors(n, v, symmetric=False, rng=rng)
+    t2 = synth.amplitudes(o, v, symmetric=True, rng=rng)
+    R_ref = oracle.ladder(L, t2)
+    R = _fwd(L, t2, dev, mode=mode, symmetric=True, a_block=a_block, order="integral_first")
+    assert rel(R, R_ref) < TOL[mode], (mode, a_block, rel(R, R_ref))
+    if mode != "fp64":
+        # R[i,j,a,b] and R[j,i,b,a] are written from one value
+        assert np.array_equal(R, R.transpose(1, 0, 3, 2))
+
+
+@pytest.mark.parametrize("o,v,n", [(1, 9, 5), (3, 1, 4), (2, 2, 3), (1, 1, 1), (6, 65, 17)])
+def test_pair_symmetric_degenerate_shapes(dev, oracle, o, v, n):
+    """o = 1 (no i < j pairs), v = 1 (no c < d entries), and tiny shapes."""
+    rng = np.random.default_rng(o * 100 + v)
+    L = synth.cholesky_vectors(n, v, symmetric=False, rng=rng)
+    t2 = synth.amplitudes(o, v, symmetric=True, rng=rng)
+    R_ref = oracle.ladder(L, t2)
+    for mode in ("ozaki_bf16", "tf32"):
+        R = _fwd(L, t2, dev, mode=mode, symmetric=True)
+        assert rel(R, R_ref) < TOL[mode], (mode, rel(R, R_ref))
+
+
 @pytest.mark.parametrize("mode", ["fp64", "ozaki_bf16"])
 def test_flags_accumulate_exchange_energy(dev, oracle, mode):
     o, v, n = 3, 29, 41
