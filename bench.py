@@ -283,9 +283,12 @@ def run_ours(a):
         B.ladder_forward(Lg, tg, R=R64, mode="fp64", symmetric=True, a_range=(0, nb), workspace=ws)
         f1.record(stream)
         torch.cuda.synchronize(dev)
-        t64 = f0.elapsed_time(f1) / 1e3 * v / nb
+        # the range's share of the work: integrals and ladder columns exist for b >= a only
+        full = B.plan(o, v, n, ws_bytes=ws_bytes, mode="fp64", symmetric=True)["flops_issued"]
+        part = B.plan(o, v, n, ws_bytes=ws_bytes, mode="fp64", symmetric=True, a_range=(0, nb))["flops_issued"]
+        t64 = f0.elapsed_time(f1) / 1e3 * full / part
         modes["fp64"] = {"tflops": flops / t64 / 1e12, "rel_err": rel(R64.cpu().numpy()),
-                         "timed_on": f"a in [0,{nb}) of {v}, scaled by {v}/{nb}"}
+                         "timed_on": f"a in [0,{nb}) of {v}, scaled by the issued-flop ratio {full / part:.2f}"}
         for m in a.other_modes.split(","):
             if not m:
                 continue

@@ -81,11 +81,11 @@ enum cc_order {
 enum cc_flags {
     CC_FLAG_ACCUMULATE = 1,     /* R += term (the paper's `t_new += ...`, Section 3) instead of R = term */
     CC_FLAG_SYMMETRIC_T = 2,    /* caller promises t2[i,j,c,d] == t2[j,i,d,c], so R[j,i,b,a] = R[i,j,a,b].
-                                   Tensor-core modes, integral-first: the integrals are built for b >= a
-                                   only ((ac|bd) = (bd|ac) holds for any L) and the ladder GEMM runs on
-                                   the parts of t2 and (ac|bd) symmetric / antisymmetric in c <-> d,
-                                   packed over c <= d (about half the flops).  FP64 mode and the
-                                   Cholesky-first order compute the pairs i <= j and mirror them.    */
+                                   Integral-first (every mode): the integrals are built for b >= a only
+                                   ((ac|bd) = (bd|ac) holds for any L) and the ladder GEMM runs on the
+                                   parts of t2 and (ac|bd) symmetric / antisymmetric in c <-> d, packed
+                                   over c <= d (about half the flops).  The Cholesky-first order
+                                   computes the pairs i <= j and mirrors them.                         */
     CC_FLAG_EXCHANGE = 4,       /* evaluate the exchange partner of Eq. 7 instead:
                                    R[i,j,a,b] = sum_cd (sum_P L_Pad L_Pbc) t2[i,j,c,d]                */
     CC_FLAG_NO_STATUS_SYNC = 8  /* do not synchronise the stream at the end; device-side failures are
@@ -110,10 +110,9 @@ typedef struct cc_ladder_args {
     void* stream;          /* cudaStream_t                                                      */
     int a_lo, a_hi;        /* range of virtual indices `a` to compute (both 0 = all of 0..v-1).
                               Entries written: R[i,j,a,b] for a in [a_lo, a_hi).  With
-                              CC_FLAG_SYMMETRIC_T: in the tensor-core modes integral-first,
-                              R[i,j,a,b] and R[i,j,b,a] for all i, j, a in the range and b >= a;
-                              otherwise R[i,j,a,b] (i <= j) and R[j,i,b,a] (i < j) for a in the
-                              range.  Either way disjoint ranges write disjoint entries, so ranges
+                              CC_FLAG_SYMMETRIC_T, integral-first: R[i,j,a,b] and R[i,j,b,a] for
+                              all i, j, a in the range and b >= a; Cholesky-first: R[i,j,a,b]
+                              (i <= j) and R[j,i,b,a] (i < j) for a in the range.  Either way disjoint ranges write disjoint entries, so ranges
                               spread over devices (each R zeroed first) assemble R by a sum.
                               energy must be NULL unless the range is complete.                  */
 } cc_ladder_args;

@@ -115,8 +115,9 @@ FwdLayout layout_packed(const Ctx& c, long long P)
     FwdLayout L{};
     Carve cv;
     const long long o = c.o, v = c.v, n = c.n, vv = v * v;
-    const int es = esz_of(c.mode);
-    const long long s = c.s;
+    const bool f64 = c.mode == CC_FP64;  // packed operands stay FP64 (DMMA), no slices
+    const int es = f64 ? 8 : esz_of(c.mode);
+    const long long s = f64 ? 1 : c.s;
     L.status = cv.take(256);
     L.pairtab = cv.take(8 * c.pp);
     L.pairtab_m = cv.take(8 * std::max(1ll, c.pm));
@@ -124,9 +125,11 @@ FwdLayout layout_packed(const Ctx& c, long long P)
     L.epart = cv.take(8 * energy_scratch_doubles(c.o, c.v));
     L.epair = cv.take(8 * o * o);
     L.V = cv.take(8 * P * vv);
-    L.Lw = cv.take(es * s * vv * pitch_for(n, es));
-    L.eL = cv.take(4 * vv);
-    L.colmax = cv.take(8 * vv);
+    if (!f64) {
+        L.Lw = cv.take(es * s * vv * pitch_for(n, es));
+        L.eL = cv.take(4 * vv);
+        L.colmax = cv.take(8 * vv);
+    }
     L.Tp = cv.take(es * s * c.pp * pitch_for(c.Kp, es));
     L.eTp = cv.take(4 * c.pp);
     L.Tm = cv.take(es * s * c.pm * pitch_for(c.Km, es));
@@ -315,7 +318,7 @@ int make_ctx(const cc_ladder_args* a, Ctx* c)
     c->Km = (long long)a->v * (a->v - 1) / 2;
     // the packed path needs the pair symmetry and runs the tensor-core modes integral-first;
     // the order's cost model sees the packed flop count
-    const bool can_pack = c->sym && is_tc(a->mode);
+    const bool can_pack = c->sym;
     c->packed = can_pack;
     c->order = pick_order(*c, a->order);
     c->packed = can_pack && c->order == CC_ORDER_INTEGRAL_FIRST;
@@ -326,9 +329,9 @@ bool aligned(const void* p, size_t al) { return ((uintptr_t)p % al) == 0; }
 
 int check_cuda(cudaError_t e) { return e == cudaSuccess ? CC_OK : CC_ERR_CUDA; }
 
-int run_f64(const char* name, const GemmF64& g, cudaStream_t st)
+int run_f64(const char* name, const GemmF64& g, cudaStream_t st, double elems = -1.0)
 {
-    ProfScope ps(name, st, 2.0 * g.M * (double)g.N * g.K);
+    ProfScope ps(name, st, 2.0 * (elems >= 0 ? elems : g.M * (double)g.N) * g.K);
     return check_cuda(gemm_f64(g, st));
 }
 
@@ -388,11 +391,10 @@ double tc_products(const Ctx& c) { return c.mode == CC_OZAKI_BF16 ? c.s * (c.s +
 
 // Output elements of an M x N slice GEMM that lie in tiles the triangular skip keeps
 // (a(m) = m / tri, b(n) = n / tri; a tile goes when b < a for all its elements).
-// Tile edges as in gemm_tc.cu (128 x 256).
-double tri_elems(long long M, long long N, long long tri)
+// Tile edges TM x TN: 128 x 256 in gemm_tc.cu, 64 x 64 in gemm_f64.cu.
+double tri_elems(long long M, long long N, long long tri, long long TM = 128, long long TN = 256)
 {
     if (tri <= 0) return (double)M * N;
-    constexpr long long TM = 128, TN = 256;
     double e = 0.0;
     for (long long m0 = 0; m0 < M; m0 += TM) {
         const long long need = (m0 / tri) * tri;  // smallest n whose b reaches a(m0)
@@ -477,9 +479,9 @@ int fwd_packed(const Ctx& c, const cc_ladder_args* a, const double* Lsrc, const 
                const FwdLayout& Lo, void* ws, int* status, cudaStream_t st, int alo, int ahi)
 {
     const long long v = c.v, n = c.n, vv = v * v;
-    const bool ozaki = c.mode == CC_OZAKI_BF16;
-    const int kind = ozaki ? 0 : (c.mode == CC_BF16 ? 1 : 2);
-    const int es = esz_of(c.mode);
+    const bool ozaki = c.mode == CC_OZAKI_BF16, f64 = c.mode == CC_FP64;
+    const int kind = ozaki ? 0 : (c.mode == CC_BF16 ? 1 : (f64 ? 3 : 2));
+    const int es = f64 ? 8 : esz_of(c.mode);
     long long* pairtab = at<long long>(ws, Lo.pairtab);
     long long* pairtab_m = at<long long>(ws, Lo.pairtab_m);
     long long* rtab = at<long long>(ws, Lo.rtab);
@@ -494,9 +496,11 @@ int fwd_packed(const Ctx& c, const cc_ladder_args* a, const double* Lsrc, const 
     Vp.D = at<void>(ws, Lo.Vp); Vp.e = at<int>(ws, Lo.eVp); Vp.pitch = Tp.pitch;
     Vm.D = at<void>(ws, Lo.Vm); Vm.e = at<int>(ws, Lo.eVm); Vm.pitch = Tm.pitch;
     {
-        // L rows (a,c) are contiguous in L[P][a][c]; K = P is strided
-        ColSrc ls{Lsrc, vv, vv, n, 0, plain_map(0)};
-        CC_TRY(prep_cols(c, ls, Lw, at<unsigned long long>(ws, Lo.colmax), st));
+        if (!f64) {
+            // L rows (a,c) are contiguous in L[P][a][c]; K = P is strided
+            ColSrc ls{Lsrc, vv, vv, n, 0, plain_map(0)};
+            CC_TRY(prep_cols(c, ls, Lw, at<unsigned long long>(ws, Lo.colmax), st));
+        }
         ProfScope ps("split", st);
         CC_CU(pm_split_f64(t2, pairtab, 1, c.pp, c.v, +1, 1.0, kind, c.s, kBeta, Tp.D, Tp.pitch, Tp.e, st));
         if (minus)
@@ -511,8 +515,18 @@ int fwd_packed(const Ctx& c, const cc_ladder_args* a, const double* Lsrc, const 
         const long long nr = (long long)Ab * Nb - (long long)Ab * (Ab - 1) / 2;
         // KG1: V[al][b'][c][d] = sum_P L[P, a0+al, c] L[P, a0+b', d], tiles with b < a skipped
         OutDesc o1{V, split_map(v, (long long)Nb * vv, v), split_map(v, vv, 1), 0};
-        CC_TRY(run_tc("kg1_tc", c, Ab * c.v, Nb * c.v, c.n, Lw, (long long)a0 * v, Lw, (long long)a0 * v, o1, status,
-                      st, true, v));
+        if (f64) {
+            GemmF64 g{};
+            g.M = Ab * c.v; g.N = Nb * c.v; g.K = c.n;
+            g.A = Lsrc; g.am = plain_map(1, (long long)a0 * v); g.ak = plain_map(vv);
+            g.B = Lsrc; g.bm = plain_map(1, (long long)a0 * v); g.bk = plain_map(vv);
+            g.out = o1;
+            g.tri = v;
+            CC_TRY(run_f64("kg1_f64", g, st, tri_elems(g.M, g.N, v, 64, 64)));
+        } else {
+            CC_TRY(run_tc("kg1_tc", c, Ab * c.v, Nb * c.v, c.n, Lw, (long long)a0 * v, Lw, (long long)a0 * v, o1,
+                          status, st, true, v));
+        }
         CC_CU(fill_rtab(Ab, Nb, rtab, st));
         Vp.rows = nr; Vm.rows = nr;
         {
@@ -529,10 +543,21 @@ int fwd_packed(const Ctx& c, const cc_ladder_args* a, const double* Lsrc, const 
             }
         }
         OutDesc op{Rpc, plain_map(nr), plain_map(1), 0};
-        CC_TRY(run_tc("kg2_tc", c, (int)c.pp, (int)nr, (int)c.Kp, Tp, 0, Vp, 0, op, status, st));
-        if (minus) {
-            OutDesc om{Rmc, plain_map(nr), plain_map(1), 0};
-            CC_TRY(run_tc("kg2_tc", c, (int)c.pm, (int)nr, (int)c.Km, Tm, 0, Vm, 0, om, status, st));
+        OutDesc om{Rmc, plain_map(nr), plain_map(1), 0};
+        if (f64) {
+            for (int sg = 0; sg < (minus ? 2 : 1); ++sg) {
+                const Operand& T = sg ? Tm : Tp;
+                const Operand& Vx = sg ? Vm : Vp;
+                GemmF64 g{};
+                g.M = (int)(sg ? c.pm : c.pp); g.N = (int)nr; g.K = (int)(sg ? c.Km : c.Kp);
+                g.A = (const double*)T.D; g.am = plain_map(T.pitch); g.ak = plain_map(1);
+                g.B = (const double*)Vx.D; g.bm = plain_map(Vx.pitch); g.bk = plain_map(1);
+                g.out = sg ? om : op;
+                CC_TRY(run_f64("kg2_f64", g, st));
+            }
+        } else {
+            CC_TRY(run_tc("kg2_tc", c, (int)c.pp, (int)nr, (int)c.Kp, Tp, 0, Vp, 0, op, status, st));
+            if (minus) CC_TRY(run_tc("kg2_tc", c, (int)c.pm, (int)nr, (int)c.Km, Tm, 0, Vm, 0, om, status, st));
         }
         ProfScope ps("scatter", st);
         CC_CU(pm_combine(c.o, c.v, a0, Ab, Nb, nr, Rpc, minus ? Rmc : nullptr, a->R, accum, st));
@@ -962,7 +987,9 @@ int cc_ladder_plan_query(const cc_ladder_args* args, cc_ladder_plan* plan)
         for (const auto& b : blocks) {
             const long long Ab = b.second, Nb = c.v - b.first;
             const double nr = (double)Ab * Nb - (double)Ab * (Ab - 1) / 2;
-            issued += 2.0 * c.n * tri_elems(Ab * c.v, Nb * c.v, c.v) + 2.0 * nr * ((double)c.pp * c.Kp + (double)c.pm * c.Km);
+            const double e1 = c.mode == CC_FP64 ? tri_elems(Ab * c.v, Nb * c.v, c.v, 64, 64)
+                                                : tri_elems(Ab * c.v, Nb * c.v, c.v);
+            issued += 2.0 * c.n * e1 + 2.0 * nr * ((double)c.pp * c.Kp + (double)c.pm * c.Km);
         }
     } else {
         issued = (c.order == CC_ORDER_INTEGRAL_FIRST ? 2.0 * ((double)c.pairs + c.n) * v * v * v * v

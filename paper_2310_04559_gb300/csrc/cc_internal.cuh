@@ -52,6 +52,7 @@ struct GemmF64 {
     const double* A; Map2 am, ak;
     const double* B; Map2 bm, bk;
     OutDesc out;
+    long long tri;  // triangular tile skip (0 = off): tiles with n / tri < m / tri everywhere are skipped
 };
 cudaError_t gemm_f64(const GemmF64& g, cudaStream_t s);
 
@@ -131,7 +132,7 @@ cudaError_t split_fixed_rows_bf16(const FixedSrc& src, int s, int beta, void* D,
 // Packed rows of an FP64 source: row r is the v x v matrix at X + (rowtab ? rowtab[r] : r) * rowmul;
 // sign > 0 writes the c <= d part (X[c][d] + X[d][c]) * h (diagonal X[c][c]) at c*v - c(c-1)/2 + d - c,
 // sign < 0 the c < d part (X[c][d] - X[d][c]) * h at c*(v-1) - c(c-1)/2 + d - c - 1.  kind 0: Ozaki
-// digits with a row exponent, 1: bf16 copy (e = 0), 2: tf32 copy (e may be NULL).
+// digits with a row exponent, 1: bf16 copy (e = 0), 2: tf32 copy (e may be NULL), 3: FP64 copy.
 cudaError_t pm_split_f64(const double* X, const long long* rowtab, long long rowmul, long long rows, int v, int sign,
                          double h, int kind, int s, int beta, void* D, long long pitch, int* e, cudaStream_t st);
 // Int64 fixed-point integral block: packed row r is unpacked row ru = rtab[r] of X (ldx per row),

@@ -59,6 +59,7 @@ __global__ void __launch_bounds__(THREADS) gemm_f64_kernel(const GemmF64 g)
     __shared__ double Bs[2][BKT][BN + 1];
 
     const int m0 = blockIdx.y * BM, n0 = blockIdx.x * BN;
+    if (g.tri > 0 && (long long)min(g.N - 1, n0 + BN - 1) / g.tri < (long long)m0 / g.tri) return;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int wm = (warp >> 1) * 32, wn = (warp & 1) * 32;
 

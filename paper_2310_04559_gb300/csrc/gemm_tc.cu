@@ -32,10 +32,12 @@
 //            accumulation into caller data).  Single-level passes alternate the
 //            two accumulators so the MMAs of pass p+1 overlap the drain of pass p.
 //
-// Warp roles (224 threads): warp 0 TMA producer, warps 1-2 MMA issuers
-// (tcgen05.mma.cta_group::1, M=128, N=256; warp 1 also allocates TMEM), warps 3..6 epilogue
-// (tcgen05.ld 32 lanes x 32 columns, transpose through shared memory, coalesced
-// global read-modify-write).  CTAs are rastered in groups of M-tiles so the
+// Warp roles (352 threads): warp 0 TMA producer, warps 1-2 MMA issuers
+// (tcgen05.mma.cta_group::1, M=128, N=256; warp 1 also allocates TMEM), warps 3..10 epilogue:
+// two warps per TMEM lane quarter, each owning one half of the tile's columns (tcgen05.ld of
+// 32 lanes x 16 columns, transpose through shared memory, global accesses of two rows x 128
+// contiguous bytes per instruction).  The epilogue of a pass keeps the MMA warps waiting, so
+// it is kept short: both levels of a pair are combined into one int64 per element.  CTAs are rastered in groups of M-tiles so the
 // CTAs resident at once share their A and B tiles in L2.
 //
 // Every mbarrier wait is bounded (globaltimer); on expiry the CTA raises a
@@ -61,7 +63,7 @@ constexpr int NA = 4, NB = 4;                  // A ring and B ring slots (power
 static_assert((NA & (NA - 1)) == 0 && (NB & (NB - 1)) == 0, "ring sizes must be powers of two");
 constexpr int TILE_SMEM = NA * A_TILE + NB * B_TILE;  // 192 KB
 constexpr int MAX_SLICES = 8;
-constexpr int EPI_WARPS = 4;
+constexpr int EPI_WARPS = 8;                   // two per TMEM lane quarter
 constexpr int ISSUERS = 2;                     // MMA-issuing warps (one per level of a pair)
 constexpr int THREADS = 32 * (1 + ISSUERS + EPI_WARPS);
 constexpr int TMEM_COLS = 512;
@@ -77,7 +79,7 @@ struct SmemCtl {
     long long rowoff[BM];
     int eA[BM];
     int eB[BN];
-    float stage[EPI_WARPS][32][33];
+    float stage[EPI_WARPS][32][17];
 };
 constexpr size_t SMEM_BYTES = 1024 + TILE_SMEM + sizeof(SmemCtl);
 
@@ -267,6 +269,19 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32])
     asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 #pragma unroll
     for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16])
+{
+    uint32_t r[16];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+        : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+    for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
 }
 
 __device__ __forceinline__ double pow2(int e)
@@ -550,14 +565,32 @@ gemm_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
         }
     } else {
         // ------------------------------------------------------------ epilogue
-        const int q4 = warp & 3;  // TMEM lane quarter this warp may access
+        // Warp e = warp - 1 - ISSUERS may read TMEM lanes 32 (warp % 4) .. + 31 (rows row0..) and
+        // owns columns half*128 .. +127 of the tile, in sub-chunks of 16 columns.  A sub-chunk
+        // of one level is read lane = row, staged, and re-read lane = column: lane L handles
+        // column cl = L % 16 of rows 2k + rp (rp = L / 16, k < 16).
+        const int e = warp - 1 - ISSUERS;
+        const int q4 = warp & 3;
         const int row0 = q4 * 32;
-        float(*stg)[33] = ctl->stage[warp - 1 - ISSUERS];
+        const int half = e >> 2;
+        const int cl = lane & 15, rp = lane >> 4;
+        float(*stg)[17] = ctl->stage[e];
         uint32_t tuse0 = 0, tuse1 = 0;
         int toggle = 0;
         PassIter it;
         it.begin(p, split);
         bool ok = true;
+        // one level of one sub-chunk: a[k] = acc(row0 + 2k + rp, col + cl)
+        auto load_level = [&](uint32_t taddr, float (&a)[16]) {
+            float v[16];
+            tmem_ld16(taddr, v);
+#pragma unroll
+            for (int j = 0; j < 16; ++j) stg[lane][j] = v[j];
+            __syncwarp();
+#pragma unroll
+            for (int k = 0; k < 16; ++k) a[k] = stg[2 * k + rp][cl];
+            __syncwarp();
+        };
         do {
             const int L1 = p.glo[it.g], nl = p.gn[it.g];
             // buffer of level L1 + q is (q ? 1 : buf0)
@@ -570,78 +603,86 @@ gemm_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
             if (!ok) break;
             fence_after();
             const bool first = it.idx == 0, last = it.last(p);
-            for (int c = 0; c < BN / 32; ++c) {
-                const int n = n0 + c * 32 + lane;
+            const uint32_t tl = tmem + ((uint32_t)row0 << 16);
+            for (int sc = 0; sc < BN / 32; ++sc) {
+                const int col = half * (BN / 2) + sc * 16;  // tile column of the sub-chunk
+                const int n = n0 + col + cl;
                 const bool ncol = n < p.N;
                 const long long co = ncol ? map2(p.out.cmap, n) : 0;
+                float a0[16], a1[16];
+                load_level(tl + (uint32_t)(buf0 * BN + col), a0);
+                if (nb == 2) load_level(tl + (uint32_t)(BN + col), a1);
                 if (p.epi != EPI_FP64_RMW) {
-                    long long X[32];
+                    // exact int64 fixed point (2^-fixF of a level-0 unit); a level pair is combined
+                    // as (acc_L1 * 2^beta + acc_L2) before the one shift to the fixed-point scale
+                    long long X[16];
+                    const int sh = p.fixF - p.beta * (L1 + nb - 1);
+                    if (nb == 2) {
 #pragma unroll
-                    for (int r = 0; r < 32; ++r) X[r] = 0;
-                    for (int q = 0; q < nb; ++q) {
-                        float v[32];
-                        tmem_ld32(tmem + ((uint32_t)row0 << 16) + (uint32_t)((q ? 1 : buf0) * BN + c * 32), v);
+                        for (int k = 0; k < 16; ++k)
+                            X[k] = ((long long)__float2int_rn(a0[k]) << p.beta) + (long long)__float2int_rn(a1[k]);
+                    } else {
 #pragma unroll
-                        for (int j = 0; j < 32; ++j) stg[lane][j] = v[j];
-                        __syncwarp();
-                        const int sh = p.fixF - p.beta * (L1 + q);
-#pragma unroll
-                        for (int r = 0; r < 32; ++r) X[r] += fix_shift(__float2int_rn(stg[r][lane]), sh);
-                        __syncwarp();
+                        for (int k = 0; k < 16; ++k) X[k] = (long long)__float2int_rn(a0[k]);
                     }
-                    const int eb = ctl->eB[c * 32 + lane] + p.scale_base - p.fixF;
+                    if (sh >= 0) {
+#pragma unroll
+                        for (int k = 0; k < 16; ++k) X[k] <<= sh;
+                    } else {
+                        const long long rnd = 1ll << (-sh - 1);
+#pragma unroll
+                        for (int k = 0; k < 16; ++k) X[k] = (X[k] + rnd) >> (-sh);
+                    }
                     if (p.epi == EPI_FIXED64_RED || p.epi == EPI_FIXED64_ADD) {
                         // int64 result for a consumer that scales it: store (first pass of an
                         // unsplit tile), then add without reading
                         const bool store = first && p.epi == EPI_FIXED64_RED;
 #pragma unroll
-                        for (int r = 0; r < 32; ++r) {
-                            const long long ro = ctl->rowoff[row0 + r];
+                        for (int k = 0; k < 16; ++k) {
+                            const long long ro = ctl->rowoff[row0 + 2 * k + rp];
                             if (ro < 0 || !ncol) continue;
                             unsigned long long* dst = (unsigned long long*)(p.out.C + ro + co);
-                            if (store) __stcg((long long*)dst, X[r]);
-                            else atomicAdd(dst, (unsigned long long)X[r]);
+                            if (store) __stcg((long long*)dst, X[k]);
+                            else atomicAdd(dst, (unsigned long long)X[k]);
                         }
                         continue;
                     }
-                    // all loads of the chunk are issued before any store (no aliasing stalls)
+                    // all loads of the sub-chunk are issued before any store (no aliasing stalls)
                     if (!first) {
 #pragma unroll
-                        for (int r = 0; r < 32; ++r) {
-                            const long long ro = ctl->rowoff[row0 + r];
-                            if (ro >= 0 && ncol) X[r] += __ldcg((const long long*)(p.out.C + ro + co));
+                        for (int k = 0; k < 16; ++k) {
+                            const long long ro = ctl->rowoff[row0 + 2 * k + rp];
+                            if (ro >= 0 && ncol) X[k] += __ldcg((const long long*)(p.out.C + ro + co));
                         }
                     }
+                    const int eb = ctl->eB[col + cl] + p.scale_base - p.fixF;
 #pragma unroll
-                    for (int r = 0; r < 32; ++r) {
-                        const long long ro = ctl->rowoff[row0 + r];
+                    for (int k = 0; k < 16; ++k) {
+                        const int r = row0 + 2 * k + rp;
+                        const long long ro = ctl->rowoff[r];
                         if (ro < 0 || !ncol) continue;
                         long long* dst = (long long*)(p.out.C + ro + co);
-                        if (last) __stcg((double*)dst, (double)X[r] * pow2(ctl->eA[row0 + r] + eb));
-                        else __stcg(dst, X[r]);
+                        if (last) __stcg((double*)dst, (double)X[k] * pow2(ctl->eA[r] + eb));
+                        else __stcg(dst, X[k]);
                     }
                 } else {
-                    for (int q = 0; q < nb; ++q) {
-                        float v[32];
-                        tmem_ld32(tmem + ((uint32_t)row0 << 16) + (uint32_t)((q ? 1 : buf0) * BN + c * 32), v);
+                    // FP64 read-modify-write of 2^e * acc (both levels of a pair at once)
+                    const bool store_only = first && !p.out.accumulate;
+                    const int eb0 = ctl->eB[col + cl] + p.scale_base - p.beta * L1;
+                    double old[16];
 #pragma unroll
-                        for (int j = 0; j < 32; ++j) stg[lane][j] = v[j];
-                        __syncwarp();
-                        const bool store_only = first && q == 0 && !p.out.accumulate;
-                        const int eb = ctl->eB[c * 32 + lane] + p.scale_base - p.beta * (L1 + q);
-                        double old[32];
+                    for (int k = 0; k < 16; ++k) {
+                        const long long ro = ctl->rowoff[row0 + 2 * k + rp];
+                        old[k] = (!store_only && ro >= 0 && ncol) ? __ldcg(p.out.C + ro + co) : 0.0;
+                    }
 #pragma unroll
-                        for (int r = 0; r < 32; ++r) {
-                            const long long ro = ctl->rowoff[row0 + r];
-                            old[r] = (!store_only && ro >= 0 && ncol) ? __ldcg(p.out.C + ro + co) : 0.0;
-                        }
-#pragma unroll
-                        for (int r = 0; r < 32; ++r) {
-                            const long long ro = ctl->rowoff[row0 + r];
-                            if (ro < 0 || !ncol) continue;
-                            __stcg(p.out.C + ro + co, old[r] + (double)stg[r][lane] * pow2(ctl->eA[row0 + r] + eb));
-                        }
-                        __syncwarp();
+                    for (int k = 0; k < 16; ++k) {
+                        const int r = row0 + 2 * k + rp;
+                        const long long ro = ctl->rowoff[r];
+                        if (ro < 0 || !ncol) continue;
+                        double val = (double)a0[k] * pow2(ctl->eA[r] + eb0);
+                        if (nb == 2) val += (double)a1[k] * pow2(ctl->eA[r] + eb0 - p.beta);
+                        __stcg(p.out.C + ro + co, old[k] + val);
                     }
                 }
             }

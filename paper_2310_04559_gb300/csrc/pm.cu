@@ -47,17 +47,36 @@ __device__ __forceinline__ long long km_of(long long c, long long d, long long v
     return c * (v - 1) - c * (c - 1) / 2 + (d - c - 1);
 }
 
+// bf16 bit pattern of a small integer (|d| <= 256, exact): the float 1.5*2^23 + d has unit
+// spacing, so subtracting 1.5*2^23 gives d exactly, and d has at most 8 significant bits.
+__device__ __forceinline__ unsigned short bf16_small(int d)
+{
+    return (unsigned short)(__float_as_uint(__int_as_float(0x4B400000 + d) - 12582912.0f) >> 16);
+}
+
+// H = half * sum_{k<s} 2^(beta k): X + H holds the balanced digits of X plus `half` each as
+// plain base-2^beta digits (no carries to propagate), for |X| <= 2^(beta s - 1) < H.
+__device__ __forceinline__ long long digit_bias(int s, int beta)
+{
+    long long H = 0;
+    for (int k = 0; k < s; ++k) H = (H << beta) | (1ll << (beta - 1));
+    return H;
+}
+
 // Balanced base-2^beta digits of X (d_0 most significant) as bf16, same convention as
 // the row splits: x ~= sum_k d_k 2^(e - beta + 1 - beta k) for X = round(x 2^(beta s - 1 - e)).
-__device__ __forceinline__ void put_digits(long long X, int s, int beta, __nv_bfloat16* out, long long stride)
+__device__ __forceinline__ void put_digits(long long X, long long H, int s, int beta, __nv_bfloat16* out,
+                                           long long stride)
 {
-    const long long half = 1ll << (beta - 1), mask = (1ll << beta) - 1;
-    for (int k = s - 1; k > 0; --k) {
-        const long long d = ((X + half) & mask) - half;
-        X = (X - d) >> beta;
-        out[k * stride] = __float2bfloat16_rn((float)d);
+    const unsigned long long Y = (unsigned long long)(X + H);
+    const int half = 1 << (beta - 1), mask = (1 << beta) - 1;
+    unsigned short* o = (unsigned short*)out;
+    o[0] = bf16_small((int)(Y >> (beta * (s - 1))) - half);
+#pragma unroll
+    for (int k = 1; k < 8; ++k) {
+        if (k >= s) break;
+        o[k * stride] = bf16_small(((int)(Y >> (beta * (s - 1 - k))) & mask) - half);
     }
-    out[0] = __float2bfloat16_rn((float)X);
 }
 
 // X * 2^sh rounded to an integer (round half up on right shifts).
@@ -122,7 +141,8 @@ __device__ __forceinline__ double pm_value(double x1, double x2, bool diag, int 
 }
 
 // FP64 source: one row r is the v x v matrix at X + rowtab[r] * rowmul (rowtab NULL: r * rowmul).
-// kind: 0 = Ozaki digits (s slices, exponent per row), 1 = bf16 copy (e = 0), 2 = tf32 copy.
+// kind: 0 = Ozaki digits (s slices, exponent per row), 1 = bf16 copy (e = 0), 2 = tf32 copy,
+// 3 = FP64 copy.
 __global__ void pm_f64_kernel(const double* __restrict__ X0, const long long* __restrict__ rowtab, long long rowmul,
                               int v, int sign, double h, int kind, int s, int beta, void* __restrict__ D,
                               long long pitch, long long rows, int* __restrict__ e_out)
@@ -136,6 +156,7 @@ __global__ void pm_f64_kernel(const double* __restrict__ X0, const long long* __
     const long long vv = v;
     const long long slice_stride = rows * pitch;
     const int total = beta * s;
+    const long long H = kind == 0 ? digit_bias(s, beta) : 0;
     int e = 0;
     for (int pass = (kind == 0 ? 0 : 1); pass < 2; ++pass) {
         unsigned long long mx = 0;
@@ -158,9 +179,11 @@ __global__ void pm_f64_kernel(const double* __restrict__ X0, const long long* __
                         const unsigned long long b = (unsigned long long)__double_as_longlong(z) & kAbs;
                         mx = b > mx ? b : mx;
                     } else if (kind == 0) {
-                        put_digits(fixed_of(z, e, total), s, beta, (__nv_bfloat16*)D + r * pitch + k, slice_stride);
+                        put_digits(fixed_of(z, e, total), H, s, beta, (__nv_bfloat16*)D + r * pitch + k, slice_stride);
                     } else if (kind == 1) {
                         ((__nv_bfloat16*)D)[r * pitch + k] = __double2bfloat16(z);
+                    } else if (kind == 3) {
+                        ((double*)D)[r * pitch + k] = z;
                     } else {
                         ((float*)D)[r * pitch + k] = tf32_of(z);
                     }
@@ -203,13 +226,13 @@ __global__ void pm_fixed_kernel(const PmFixedSrc src, int s, int beta, __nv_bflo
     int mx = INT_MIN;
     for (int c = warp; c < v; c += 8) {
         const long long* Xc = X + c * vv;
+        const int ec = eo[c];
+#pragma unroll 4
         for (int d = lane; d < v; d += 32) {
             const long long x = __ldcs(Xc + d);
-            if (x) {
-                const unsigned long long ax = x < 0 ? (unsigned long long)(-x) : (unsigned long long)x;
-                const int b = 64 - __clzll((long long)ax) + eo[c] + ei[d];
-                mx = b > mx ? b : mx;
-            }
+            const unsigned long long ax = x < 0 ? (unsigned long long)(-x) : (unsigned long long)x;
+            const int b = x ? 64 - __clzll((long long)ax) + ec + ei[d] : INT_MIN;
+            mx = b > mx ? b : mx;
         }
     }
     for (int w = 16; w > 0; w >>= 1) mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, w));
@@ -224,35 +247,52 @@ __global__ void pm_fixed_kernel(const PmFixedSrc src, int s, int beta, __nv_bflo
         if (em) em[r] = E;
     }
     // pass 2: Y = round(V * 2^(total - E)) (one guard bit), V+- = (Y1 +- Y2) / 4 at the
-    // digit scale 2^(total - 1 - E); the diagonal of V+ is Y1 / 2
+    // digit scale 2^(total - 1 - E); the diagonal of V+ is Y1 / 2.  Tile pairs (tc <= td)
+    // in order; the next pair's loads are issued before the current pair is split.
     const int total = beta * s;
+    const long long H = digit_bias(s, beta);
     const int tx = lane, ty = warp;
     const int nt = (v + TT - 1) / TT;
     const long long sp = src.rows * pitchp, sm = src.rows * pitchm;
     const int sh0 = src.base + total - E;
-    for (int tc = 0; tc < nt; ++tc) {
-        for (int td = tc; td < nt; ++td) {
-            __syncthreads();
-            for (int y = ty; y < TT; y += TY) {
-                const int c = tc * TT + y, d = td * TT + tx;
-                S1[y][tx] = (!zero && c < v && d < v) ? __ldcs(X + c * vv + d) : 0;
-                const int d2 = td * TT + y, c2 = tc * TT + tx;
-                S2[y][tx] = (!zero && d2 < v && c2 < v) ? __ldcs(X + d2 * vv + c2) : 0;
-            }
-            __syncthreads();
-            for (int y = ty; y < TT; y += TY) {
-                const int c = tc * TT + y, d = td * TT + tx;
-                if (c >= v || d >= v || d < c) continue;
-                const long long Y1 = shr_round(S1[y][tx], eo[c] + ei[d] + sh0);
-                if (c == d) {
-                    put_digits((Y1 + 1) >> 1, s, beta, Dp + r * pitchp + kp_of(c, d, vv), sp);
-                } else {
-                    const long long Y2 = shr_round(S2[tx][y], eo[d] + ei[c] + sh0);
-                    put_digits((Y1 + Y2 + 2) >> 2, s, beta, Dp + r * pitchp + kp_of(c, d, vv), sp);
-                    if (Dm) put_digits((Y1 - Y2 + 2) >> 2, s, beta, Dm + r * pitchm + km_of(c, d, vv), sm);
-                }
+    long long q1[TT / TY], q2[TT / TY];
+    auto fetch = [&](int tc, int td) {
+#pragma unroll
+        for (int u = 0; u < TT / TY; ++u) {
+            const int y = ty + u * TY;
+            const int c = tc * TT + y, d = td * TT + tx;
+            q1[u] = (!zero && c < v && d < v) ? __ldcs(X + c * vv + d) : 0;
+            const int d2 = td * TT + y, c2 = tc * TT + tx;
+            q2[u] = (!zero && d2 < v && c2 < v) ? __ldcs(X + d2 * vv + c2) : 0;
+        }
+    };
+    int tc = 0, td = 0;
+    fetch(0, 0);
+    while (tc < nt) {
+        __syncthreads();
+#pragma unroll
+        for (int u = 0; u < TT / TY; ++u) {
+            S1[ty + u * TY][tx] = q1[u];
+            S2[ty + u * TY][tx] = q2[u];
+        }
+        __syncthreads();
+        int nc = tc, nd = td + 1;
+        if (nd == nt) { ++nc; nd = nc; }
+        if (nc < nt) fetch(nc, nd);
+        for (int y = ty; y < TT; y += TY) {
+            const int c = tc * TT + y, d = td * TT + tx;
+            if (c >= v || d >= v || d < c) continue;
+            const long long Y1 = shr_round(S1[y][tx], eo[c] + ei[d] + sh0);
+            if (c == d) {
+                put_digits((Y1 + 1) >> 1, H, s, beta, Dp + r * pitchp + kp_of(c, d, vv), sp);
+            } else {
+                const long long Y2 = shr_round(S2[tx][y], eo[d] + ei[c] + sh0);
+                put_digits((Y1 + Y2 + 2) >> 2, H, s, beta, Dp + r * pitchp + kp_of(c, d, vv), sp);
+                if (Dm) put_digits((Y1 - Y2 + 2) >> 2, H, s, beta, Dm + r * pitchm + km_of(c, d, vv), sm);
             }
         }
+        tc = nc;
+        td = nd;
     }
 }
 

@@ -56,16 +56,29 @@ __device__ __forceinline__ long long fixed_point(double x, int e, int total_bits
     return (bits >> 63) ? -X : X;
 }
 
-// Writes the s balanced base-2^beta digits of X (d_0 most significant) as bf16.
+// bf16 bit pattern of a small integer (|d| <= 256, exact): the float 1.5*2^23 + d has unit
+// spacing, so subtracting 1.5*2^23 gives d exactly, and d has at most 8 significant bits.
+__device__ __forceinline__ unsigned short bf16_small(int d)
+{
+    return (unsigned short)(__float_as_uint(__int_as_float(0x4B400000 + d) - 12582912.0f) >> 16);
+}
+
+// Writes the s balanced base-2^beta digits of X (d_0 most significant, |X| <= 2^(beta s - 1))
+// as bf16.  With H = half * sum_{k<s} 2^(beta k), X + H holds every digit plus `half` as a
+// plain base-2^beta digit, so each digit is one shift and mask (no carry chain).
 __device__ __forceinline__ void digits_bf16(long long X, int s, int beta, __nv_bfloat16* out, long long slice_stride)
 {
-    const long long half = 1ll << (beta - 1), mask = (1ll << beta) - 1;
-    for (int k = s - 1; k > 0; --k) {
-        const long long d = ((X + half) & mask) - half;
-        X = (X - d) >> beta;
-        out[k * slice_stride] = __float2bfloat16_rn((float)d);
+    long long H = 0;
+    for (int k = 0; k < s; ++k) H = (H << beta) | (1ll << (beta - 1));
+    const unsigned long long Y = (unsigned long long)(X + H);
+    const int half = 1 << (beta - 1), mask = (1 << beta) - 1;
+    unsigned short* o = (unsigned short*)out;
+    o[0] = bf16_small((int)(Y >> (beta * (s - 1))) - half);
+#pragma unroll
+    for (int k = 1; k < 8; ++k) {
+        if (k >= s) break;
+        o[k * slice_stride] = bf16_small(((int)(Y >> (beta * (s - 1 - k))) & mask) - half);
     }
-    out[0] = __float2bfloat16_rn((float)X);
 }
 
 template <int TPR>  // threads per row: 256 (one CTA per row) or 32 (one warp per row)

@@ -107,9 +107,11 @@ def test_workspace_queries_monotone_in_budget(lib):
     # ... and issue about (n + o^2/2) v^4 multiply-adds per slice product instead of 2 (n + o(o+1)/2) v^4
     unpacked = 21 * 2.0 * (820 + 2000) * 400 ** 4
     assert 0.45 < p["flops_issued"] / unpacked < 0.6
-    # FP64 (DMMA) plans keep uniform blocks
-    ws = Ld.workspace_size(40, 400, 2000, mode="fp64", symmetric=True, budget=40 << 30)
-    p = Ld.plan(40, 400, 2000, ws_bytes=ws, mode="fp64", symmetric=True)
+    # the FP64 (DMMA) mode runs the same packed plan; without pair symmetry blocks are uniform
+    p = Ld.plan(40, 400, 2000, mode="fp64", symmetric=True, budget=40 << 30)
+    assert 0.45 < p["flops_issued"] / (2.0 * (820 + 2000) * 400 ** 4) < 0.6
+    ws = Ld.workspace_size(40, 400, 2000, mode="fp64", budget=40 << 30)
+    p = Ld.plan(40, 400, 2000, ws_bytes=ws, mode="fp64")
     assert p["ws_bytes"] == ws and p["n_blocks"] * p["a_block"] >= 400
 
 
