@@ -255,46 +255,22 @@ __device__ __forceinline__ void mma_commit_mc(unsigned long long* bar, uint16_t 
 __device__ __forceinline__ void fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
 
-__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32])
+// 32 lanes x 16 columns of TMEM into registers (no wait: pair with tmem_wait_ld).
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&r)[16])
 {
-    uint32_t r[32];
-    asm volatile(
-        "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
-        "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
-        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
-          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
-          "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
-          "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
-        : "r"(taddr));
-    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-#pragma unroll
-    for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
-}
-
-__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16])
-{
-    uint32_t r[16];
     asm volatile(
         "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
         : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
           "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
         : "r"(taddr));
-    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-#pragma unroll
-    for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
 }
+
+__device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
 
 __device__ __forceinline__ double pow2(int e)
 {
     e = e < -1022 ? -1022 : (e > 1023 ? 1023 : e);
     return __longlong_as_double((long long)(e + 1023) << 52);
-}
-
-// q * 2^sh as a fixed-point integer (round half up for right shifts).
-__device__ __forceinline__ long long fix_shift(int q, int sh)
-{
-    if (sh >= 0) return (long long)q << sh;
-    return ((long long)q + (1ll << (-sh - 1))) >> (-sh);
 }
 
 // Pass sequence shared by all roles: groups in order, each cut into K-chunks, over
@@ -345,7 +321,6 @@ gemm_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
     SmemCtl* ctl = (SmemCtl*)(base + TILE_SMEM);
 
     constexpr int KSTEP = KIND == TC_BF16 ? 64 : 32;  // K elements per 128-byte row
-    constexpr int NMMA = 4;                           // MMAs (K=16 bf16 / K=8 tf32) per row
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
 
     // grouped raster over clusters: consecutive clusters walk group_m cluster-rows
@@ -580,12 +555,10 @@ gemm_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
         PassIter it;
         it.begin(p, split);
         bool ok = true;
-        // one level of one sub-chunk: a[k] = acc(row0 + 2k + rp, col + cl)
-        auto load_level = [&](uint32_t taddr, float (&a)[16]) {
-            float v[16];
-            tmem_ld16(taddr, v);
+        // one level of one sub-chunk, from registers r (lane = row) to a[k] = acc(row0 + 2k + rp, col + cl)
+        auto transpose = [&](const uint32_t (&r)[16], float (&a)[16]) {
 #pragma unroll
-            for (int j = 0; j < 16; ++j) stg[lane][j] = v[j];
+            for (int j = 0; j < 16; ++j) stg[lane][j] = __uint_as_float(r[j]);
             __syncwarp();
 #pragma unroll
             for (int k = 0; k < 16; ++k) a[k] = stg[2 * k + rp][cl];
@@ -610,8 +583,12 @@ gemm_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
                 const bool ncol = n < p.N;
                 const long long co = ncol ? map2(p.out.cmap, n) : 0;
                 float a0[16], a1[16];
-                load_level(tl + (uint32_t)(buf0 * BN + col), a0);
-                if (nb == 2) load_level(tl + (uint32_t)(BN + col), a1);
+                uint32_t r0[16], r1[16];
+                tmem_ld16(tl + (uint32_t)(buf0 * BN + col), r0);
+                if (nb == 2) tmem_ld16(tl + (uint32_t)(BN + col), r1);
+                tmem_wait_ld();
+                transpose(r0, a0);
+                if (nb == 2) transpose(r1, a1);
                 if (p.epi != EPI_FP64_RMW) {
                     // exact int64 fixed point (2^-fixF of a level-0 unit); a level pair is combined
                     // as (acc_L1 * 2^beta + acc_L2) before the one shift to the fixed-point scale
