@@ -302,6 +302,24 @@ def run_ours(a):
             modes[m] = {"tflops": flops / (g0.elapsed_time(g1) / 1e3) / 1e12, "rel_err": rel(Rm.cpu().numpy())}
         out["modes"] = modes
         out["speedup_vs_fp64_mma"] = modes[mode]["tflops"] / modes["fp64"]["tflops"]
+        # the two further Cholesky terms with the ladder's contraction (Eq. 8, Eq. 9), same workload
+        del ws, R64
+        torch.cuda.empty_cache()
+        Lov = torch.from_numpy(synth.cholesky_ov(n, o, v, seed=rank + 7)).to(dev)
+        terms = {}
+        for name, fl in (("tijbk", 2.0 * (n + o * o) * o * float(v) ** 3),
+                         ("tijkl", 2.0 * (n + o * o) * o * o * float(v) ** 2)):
+            call = (lambda: B.tijbk(Lov, Lg, tg, mode=mode, budget=40 << 30)) if name == "tijbk" else \
+                   (lambda: B.tijkl(Lov, tg, mode=mode, budget=40 << 30))
+            call()
+            h0, h1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            h0.record(stream)
+            call()
+            h1.record(stream)
+            torch.cuda.synchronize(dev)
+            ms = h0.elapsed_time(h1)
+            terms[name] = {"tflops": fl / (ms / 1e3) / 1e12, "ms": ms, "flops_algorithmic": fl}
+        out["terms"] = terms
         sample_flops = 2.0 * (o * o + n) * float(v) ** 3 * len(a_list)
         out["cpu_baseline"] = {"value": sample_flops / t_cpu / 1e12, "unit": UNIT, "cores": threads, "kind": "oracle",
                                "sample": f"R[:, :, a, :] for a in {a_list} of the same workload "

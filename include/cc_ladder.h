@@ -198,6 +198,26 @@ int cc_ladder_energy_workspace_size(int o, int v, size_t* bytes);
 int cc_ladder_energy_noalloc(int o, int v, const double* R, const double* t2, double* energy, double* e_pair,
                              void* stream);
 
+/* The two further Cholesky terms of the CCSD vector function that share the ladder's contraction
+ * (Section 6.1, Eq. 8 and Eq. 9; the paper benchmarks both as the contraction "abcd,ecfd->efab"),
+ * with Lov[P][k][c] the occupied-virtual block of the Cholesky vectors (device [n_chol][o][v]) and
+ * Lvv the virtual-virtual block (the L of cc_ladder_fwd, device [n_chol][v][v]):
+ *   CC_TERM_IJKL  Eq. 8  T[i,j,k,l] = sum_{P,c,d} Lov[P,k,c] Lov[P,l,d] t2[i,j,c,d]   T: [o][o][o][o]
+ *   CC_TERM_IJBK  Eq. 9  T[i,j,b,k] = sum_{P,c,d} Lvv[P,b,d] Lov[P,k,c] t2[i,j,c,d]   T: [o][o][v][o]
+ * Computed like the ladder, integral-first: the four-index integrals (kc|ld) or (kc|bd) are built on
+ * the device for a block of k at a time and contracted with t2 over (c,d); no symmetry is assumed.
+ * Same precision modes, conventions and error behaviour as cc_ladder_fwd (T is overwritten;
+ * Lvv may be NULL for CC_TERM_IJKL).  flags: CC_FLAG_NO_STATUS_SYNC only. */
+enum cc_term { CC_TERM_IJKL = 1, CC_TERM_IJBK = 2 };
+int cc_ladder_term_workspace_size(int which, int o, int v, int n_chol, int mode, int slices, size_t budget_bytes,
+                                  size_t* bytes);
+int cc_ladder_term(int which, int o, int v, int n_chol, const double* Lov, const double* Lvv, const double* t2,
+                   double* T, int mode, int flags, int slices, void* workspace, size_t ws_bytes, void* stream);
+int cc_ladder_tijkl(int o, int v, int n_chol, const double* Lov, const double* t2, double* T, int mode,
+                    void* workspace, size_t ws_bytes, void* stream);
+int cc_ladder_tijbk(int o, int v, int n_chol, const double* Lov, const double* Lvv, const double* t2, double* T,
+                    int mode, void* workspace, size_t ws_bytes, void* stream);
+
 /* Device status word of a workspace after calls made with CC_FLAG_NO_STATUS_SYNC
  * (synchronises `stream`; returns CC_OK or CC_ERR_DEVICE_TIMEOUT and clears the word). */
 int cc_ladder_device_status(void* workspace, void* stream);

@@ -356,3 +356,52 @@ void oracle_exchange(int o, int v, int n, const double* L, const double* t2, dou
         free(Kab);
     }
 }
+
+/*
+ * The two further Cholesky terms of the CCSD vector function that share the
+ * ladder's contraction pattern (Section 6.1, the contraction the paper benchmarks
+ * as "abcd,ecfd->efab"), with Lov[P][k][c] the occupied-virtual block of the
+ * Cholesky vectors (k occupied, c virtual):
+ *
+ *   Eq. 8   tt_ijkl = sum_{P,c,d} L^P_kc L^P_ld t_ij^cd        O(n o^4 v^2)
+ *   Eq. 9   tt_ijbk = sum_{P,c,d} L^P_bd L^P_kc t_ij^cd        O(n o^3 v^3)
+ *
+ * Both are G[i,j,p,q] = sum_{c,d} (sum_P A[P,p,c] B[P,q,d]) t2[i,j,c,d]:
+ *   tt_ijkl[i,j,k,l] = G with A = B = Lov (np = nq = o);
+ *   tt_ijbk[i,j,b,k] = G[i,j,k,b] with A = Lov (np = o), B = Lvv (nq = v).
+ * Evaluated like the ladder: for each (p, q) build the v x v slice
+ * W[c][d] = sum_P A[P,p,c] B[P,q,d] (P in increasing order), then contract it
+ * with every t_ij.  A is n x np x v, B is n x nq x v, G is o x o x np x nq.
+ */
+void oracle_general(int o, int v, int n, int np_, int nq, const double* A, const double* B,
+                    const double* t2, double* G, int nthreads)
+{
+    set_threads(nthreads);
+    const size_t vv = (size_t)v * v;
+    const long long npairs = (long long)np_ * nq;
+#pragma omp parallel
+    {
+        double* W = (double*)malloc(sizeof(double) * vv);
+#pragma omp for schedule(dynamic, 1)
+        for (long long pair = 0; pair < npairs; ++pair) {
+            const int p = (int)(pair / nq);
+            const int q = (int)(pair % nq);
+            for (size_t x = 0; x < vv; ++x) W[x] = 0.0;
+            for (int P = 0; P < n; ++P) {
+                const double* Ap = A + ((size_t)P * np_ + p) * v;
+                const double* Bq = B + ((size_t)P * nq + q) * v;
+                for (int c = 0; c < v; ++c)
+                    for (int d = 0; d < v; ++d) W[(size_t)c * v + d] += Ap[c] * Bq[d];
+            }
+            for (int i = 0; i < o; ++i)
+                for (int j = 0; j < o; ++j) {
+                    const double* tij = t2 + ((size_t)i * o + j) * vv;
+                    double s = 0.0;
+                    for (int c = 0; c < v; ++c)
+                        for (int d = 0; d < v; ++d) s += W[(size_t)c * v + d] * tij[(size_t)c * v + d];
+                    G[(((size_t)i * o + j) * np_ + p) * nq + q] = s;
+                }
+        }
+        free(W);
+    }
+}

@@ -14,6 +14,8 @@ Functions (each follows the passage cited in ladder_oracle.c):
 * ``ladder_grad(L, t2, W)`` -- dt2, dL of loss = <W, R>.
 * ``ladder_grad_entries(...)`` -- selected gradient entries.
 * ``exchange(L, t2, a_list=None)`` -- Eq. 7.
+* ``tijkl(Lov, t2)``, ``tijbk(Lov, Lvv, t2)`` -- Eq. 8 and Eq. 9 through
+  ``general(A, B, t2)``, G[i,j,p,q] = sum_cd (sum_P A[P,p,c] B[P,q,d]) t2[i,j,c,d].
 """
 from __future__ import annotations
 
@@ -58,6 +60,7 @@ def _load():
                                                                          _llp, ctypes.c_int, _dp, ctypes.c_int])
         lib.oracle_exchange.argtypes = [ctypes.c_int] * 3 + [_dp, _dp, _dp, ctypes.POINTER(ctypes.c_int),
                                                              ctypes.c_int, ctypes.c_int]
+        lib.oracle_general.argtypes = [ctypes.c_int] * 5 + [_dp, _dp, _dp, _dp, ctypes.c_int]
         lib.oracle_max_threads.restype = ctypes.c_int
         _lib = lib
     return _lib
@@ -157,3 +160,26 @@ def exchange(L, t2, a_list=None, threads=0):
         lib.oracle_exchange(o, v, n, _p(L), _p(t2), _p(X), al.ctypes.data_as(ctypes.POINTER(ctypes.c_int)),
                             al.size, threads)
     return X
+
+
+def general(A, B, t2, threads=0):
+    """G[i,j,p,q] = sum_cd (sum_P A[P,p,c] B[P,q,d]) t2[i,j,c,d]; A is n x np x v, B is n x nq x v."""
+    lib = _load()
+    A, B, t2 = _f64(A), _f64(B), _f64(t2)
+    n, np_, v = A.shape
+    n2, nq, v2 = B.shape
+    o, o2, v3, v4 = t2.shape
+    assert n == n2 and v == v2 == v3 == v4 and o == o2, (A.shape, B.shape, t2.shape)
+    G = np.empty((o, o, np_, nq))
+    lib.oracle_general(o, v, n, np_, nq, _p(A), _p(B), _p(t2), _p(G), threads)
+    return G
+
+
+def tijkl(Lov, t2, threads=0):
+    """Eq. 8: tt[i,j,k,l] = sum_{P,c,d} Lov[P,k,c] Lov[P,l,d] t2[i,j,c,d]."""
+    return general(Lov, Lov, t2, threads)
+
+
+def tijbk(Lov, Lvv, t2, threads=0):
+    """Eq. 9: tt[i,j,b,k] = sum_{P,c,d} Lvv[P,b,d] Lov[P,k,c] t2[i,j,c,d]."""
+    return np.ascontiguousarray(general(Lov, Lvv, t2, threads).transpose(0, 1, 3, 2))

@@ -64,8 +64,9 @@ SYMBOLS = [
     "cc_ladder_energy_workspace_size", "cc_ladder_device_status", "cc_ladder_set_wait_limit_ns",
     "cc_ladder_strerror", "cc_ladder_version", "cc_ladder_gemm_workspace_size", "cc_ladder_gemm",
     "cc_ladder_profile_enable", "cc_ladder_profile_read", "cc_ladder_launch_count", "cc_ladder_energy_noalloc",
-    "cc_ladder_autotune",
+    "cc_ladder_autotune", "cc_ladder_term_workspace_size", "cc_ladder_term", "cc_ladder_tijkl", "cc_ladder_tijbk",
 ]
+TERMS = {"ijkl": 1, "ijbk": 2}
 
 
 def lib_path() -> str:
@@ -106,6 +107,10 @@ def load(build_if_missing: bool = True):
     L.cc_ladder_energy_noalloc.argtypes = [_i, _i, _vp, _vp, _vp, _vp, _vp]
     L.cc_ladder_autotune.argtypes = [ctypes.POINTER(Args), ctypes.POINTER(Plan), ctypes.POINTER(ctypes.c_double),
                                       ctypes.POINTER(ctypes.c_double)]
+    L.cc_ladder_term_workspace_size.argtypes = [_i, _i, _i, _i, _i, _i, _sz, ctypes.POINTER(_sz)]
+    L.cc_ladder_term.argtypes = [_i, _i, _i, _i, _vp, _vp, _vp, _vp, _i, _i, _i, _vp, _sz, _vp]
+    L.cc_ladder_tijkl.argtypes = [_i, _i, _i, _vp, _vp, _vp, _i, _vp, _sz, _vp]
+    L.cc_ladder_tijbk.argtypes = [_i, _i, _i, _vp, _vp, _vp, _vp, _i, _vp, _sz, _vp]
     L.cc_ladder_strerror.argtypes = [_i]
     L.cc_ladder_strerror.restype = ctypes.c_char_p
     L.cc_ladder_version.restype = ctypes.c_char_p

@@ -175,6 +175,44 @@ def ladder_backward(L, t2, dR, mode="ozaki_bf16", symmetric=False, want_dL=True,
     return dL, dt2
 
 
+def term(which, Lov, t2, Lvv=None, mode="ozaki_bf16", slices=0, budget=0, T=None, workspace=None, no_sync=False):
+    """The two further Cholesky terms that share the ladder's contraction (Eq. 8, Eq. 9):
+    which="ijkl": T[i,j,k,l] = sum_{P,c,d} Lov[P,k,c] Lov[P,l,d] t2[i,j,c,d]   (o x o x o x o)
+    which="ijbk": T[i,j,b,k] = sum_{P,c,d} Lvv[P,b,d] Lov[P,k,c] t2[i,j,c,d]   (o x o x v x o)
+    Lov is n x o x v, Lvv n x v x v."""
+    lib = _lib.load()
+    w = _lib.TERMS[which]
+    n, o, v = Lov.shape
+    _check_tensor(Lov, "Lov", (n, o, v))
+    _check_tensor(t2, "t2", (o, o, v, v))
+    if w == 2:
+        _check_tensor(Lvv, "Lvv", (n, v, v))
+    shape = (o, o, o, o) if w == 1 else (o, o, v, o)
+    if T is None:
+        T = torch.empty(shape, dtype=torch.float64, device=Lov.device)
+    _check_tensor(T, "T", shape)
+    if workspace is None:
+        ws = ctypes.c_size_t()
+        _lib.check(lib.cc_ladder_term_workspace_size(w, o, v, n, _mode(mode), int(slices), int(budget),
+                                                     ctypes.byref(ws)), "cc_ladder_term_workspace_size")
+        workspace = alloc_workspace(ws.value, Lov.device)
+    st = lib.cc_ladder_term(w, o, v, n, _ptr(Lov), _ptr(Lvv) if w == 2 else None, _ptr(t2), _ptr(T), _mode(mode),
+                            _flags(no_sync=no_sync), int(slices), _ptr(workspace), workspace.numel(),
+                            _stream(Lov.device))
+    _lib.check(st, "cc_ladder_term")
+    return T
+
+
+def tijkl(Lov, t2, mode="ozaki_bf16", **kw):
+    """Eq. 8 (see term)."""
+    return term("ijkl", Lov, t2, mode=mode, **kw)
+
+
+def tijbk(Lov, Lvv, t2, mode="ozaki_bf16", **kw):
+    """Eq. 9 (see term)."""
+    return term("ijbk", Lov, t2, Lvv=Lvv, mode=mode, **kw)
+
+
 def pair_energy(R, t2, pairs=False):
     """E = sum_ijab (2 R_ijab - R_ijba) t2_ijab (and e_ij if pairs)."""
     lib = _lib.load()

@@ -728,6 +728,160 @@ int fwd_impl(const cc_ladder_args* a, const double* Lsrc_override = nullptr)
     return finish(status, c.flags, st);
 }
 
+// ------------------------------------------------- two-block terms (Eq. 8, 9)
+// G[i,j,p,q] = sum_cd (sum_P A[P,p,c] B[P,q,d]) t2[i,j,c,d], A: n x np x v, B: n x nq x v, the
+// contraction shared by the ladder and the two further Cholesky terms of Section 6.1:
+//   Eq. 8  tt_ijkl: A = B = Lov (np = nq = o),   Eq. 9  tt_ijbk: A = Lov, B = Lvv (output [i][j][b][k]).
+// Integral-first in blocks of p, exactly like the ladder's unpacked path:
+//   KG1  V[pl][q][c][d] = sum_P A[P,p0+pl,c] B[P,q,d]    (GEMM M = Pb v, N = nq v, K = n)
+//   KG2  G[ij][p0+pl][q] = sum_(c,d) t2[ij,c,d] V[pl][q][c][d]  (GEMM M = o^2, N = Pb nq, K = v^2)
+struct TermCtx {
+    Ctx c;           // o, v, n, mode, s (pairs = o^2, no symmetry)
+    int np_, nq;
+    bool same;       // A and B are the same array (one set of slices)
+    int which;
+};
+
+struct TermLayout {
+    size_t status, V, Aw, eA, Bw, eB, colmax, tw, et, Vw, eV, total;
+};
+
+TermLayout layout_term(const TermCtx& tc, long long Pb)
+{
+    const Ctx& c = tc.c;
+    TermLayout L{};
+    Carve cv;
+    const long long o = c.o, v = c.v, n = c.n, vv = v * v;
+    L.status = cv.take(256);
+    L.V = cv.take(8 * Pb * tc.nq * vv);
+    if (is_tc(c.mode)) {
+        const int es = esz_of(c.mode);
+        const long long s = c.s;
+        L.Aw = cv.take(es * s * tc.np_ * v * pitch_for(n, es));
+        L.eA = cv.take(4 * tc.np_ * v);
+        if (!tc.same) {
+            L.Bw = cv.take(es * s * tc.nq * v * pitch_for(n, es));
+            L.eB = cv.take(4 * tc.nq * v);
+        }
+        L.colmax = cv.take(8 * std::max(tc.np_, tc.nq) * v);
+        L.tw = cv.take(es * s * o * o * pitch_for(vv, es));
+        L.et = cv.take(4 * o * o);
+        L.Vw = cv.take(es * s * Pb * tc.nq * pitch_for(vv, es));
+        L.eV = cv.take(4 * Pb * tc.nq);
+    }
+    L.total = cv.cur;
+    return L;
+}
+
+int term_ctx(int which, int o, int v, int n, int mode, int slices, TermCtx* tc)
+{
+    if (which != CC_TERM_IJKL && which != CC_TERM_IJBK) return CC_ERR_ARG;
+    cc_ladder_args a{};
+    a.o = o; a.v = v; a.n_chol = n; a.mode = mode; a.slices = slices; a.order = CC_ORDER_INTEGRAL_FIRST;
+    CC_TRY(make_ctx(&a, &tc->c));
+    if ((double)o * o * o * v > 4.0e12 || (double)n * o * v > 4.0e12) return CC_ERR_SHAPE;
+    tc->which = which;
+    tc->np_ = o;
+    tc->nq = which == CC_TERM_IJKL ? o : v;
+    tc->same = which == CC_TERM_IJKL;
+    return CC_OK;
+}
+
+// Largest block of p fitting `bytes` (-1 if one p does not fit), evened over the blocks.
+long long pick_term_block(const TermCtx& tc, size_t bytes, size_t* need)
+{
+    if (layout_term(tc, 1).total > bytes) { *need = layout_term(tc, 1).total; return -1; }
+    long long lo = 1, hi = tc.np_;
+    while (lo < hi) {
+        const long long mid = (lo + hi + 1) / 2;
+        if (layout_term(tc, mid).total <= bytes) lo = mid; else hi = mid - 1;
+    }
+    const long long nb = (tc.np_ + lo - 1) / lo;
+    const long long P = (tc.np_ + nb - 1) / nb;
+    *need = layout_term(tc, P).total;
+    return P;
+}
+
+int term_impl(int which, int o, int v, int n, const double* Lov, const double* Lvv, const double* t2, double* T,
+              int mode, int flags, int slices, void* ws, size_t ws_bytes, void* stream)
+{
+    TermCtx tc;
+    CC_TRY(term_ctx(which, o, v, n, mode, slices, &tc));
+    if (flags & ~CC_FLAG_NO_STATUS_SYNC) return CC_ERR_ARG;
+    const double* A = Lov;
+    const double* Bm = which == CC_TERM_IJKL ? Lov : Lvv;
+    if (!A || !Bm || !t2 || !T || !ws) return CC_ERR_NULL;
+    if (!aligned(A, 16) || !aligned(Bm, 16) || !aligned(t2, 16) || !aligned(T, 16) || !aligned(ws, 256))
+        return CC_ERR_ALIGN;
+    const Ctx& c = tc.c;
+    if (is_tc(c.mode) && !tc_gemm_available()) return CC_ERR_UNSUPPORTED;
+    size_t need = 0;
+    const long long Pb = pick_term_block(tc, ws_bytes, &need);
+    if (Pb < 0 || need > ws_bytes) return CC_ERR_WORKSPACE;
+    const TermLayout Lo = layout_term(tc, Pb);
+    cudaStream_t st = (cudaStream_t)stream;
+    const long long v_ = v, vv = v_ * v, np_ = tc.np_, nq = tc.nq;
+    int* status = at<int>(ws, Lo.status);
+    CC_CU(cudaMemsetAsync(status, 0, 256, st));
+    double* V = at<double>(ws, Lo.V);
+    Operand Aw{}, Bw{}, tw{}, Vw{};
+    if (is_tc(c.mode)) {
+        Aw.D = at<void>(ws, Lo.Aw); Aw.e = at<int>(ws, Lo.eA);
+        tw.D = at<void>(ws, Lo.tw); tw.e = at<int>(ws, Lo.et);
+        Vw.D = at<void>(ws, Lo.Vw); Vw.e = at<int>(ws, Lo.eV);
+        // rows (p, c) of A[P][p][c] are contiguous; K = P is strided
+        ColSrc as{A, np_ * v_, np_ * v_, n, 0, plain_map(0)};
+        CC_TRY(prep_cols(c, as, Aw, at<unsigned long long>(ws, Lo.colmax), st));
+        if (tc.same) {
+            Bw = Aw;
+        } else {
+            Bw.D = at<void>(ws, Lo.Bw); Bw.e = at<int>(ws, Lo.eB);
+            ColSrc bs{Bm, nq * v_, nq * v_, n, 0, plain_map(0)};
+            CC_TRY(prep_cols(c, bs, Bw, at<unsigned long long>(ws, Lo.colmax), st));
+        }
+        RowSrc ts{t2, plain_map(vv), plain_map(1), (long long)o * o, vv};
+        CC_TRY(prep_rows(c, ts, tw, st));
+    }
+    for (long long p0 = 0; p0 < np_; p0 += Pb) {
+        const int Ab = (int)std::min(Pb, np_ - p0);
+        // KG1: V[pl][q][c][d], GEMM rows (pl, c), cols (q, d)
+        OutDesc o1{V, split_map(v_, nq * vv, v_), split_map(v_, vv, 1), 0};
+        if (c.mode == CC_FP64) {
+            GemmF64 g{};
+            g.M = Ab * v; g.N = (int)(nq * v_); g.K = n;
+            g.A = A; g.am = plain_map(1, p0 * v_); g.ak = plain_map(np_ * v_);
+            g.B = Bm; g.bm = plain_map(1); g.bk = plain_map(nq * v_);
+            g.out = o1;
+            CC_TRY(run_f64("term_kg1_f64", g, st));
+        } else {
+            CC_TRY(run_tc("term_kg1_tc", c, Ab * v, (int)(nq * v_), n, Aw, p0 * v_, Bw, 0, o1, status, st, true));
+        }
+        // KG2: T[ij][p0 + pl][q] (Eq. 8: [i][j][k][l]) or T[ij][q][p0 + pl] (Eq. 9: [i][j][b][k])
+        const Map2 ocol = which == CC_TERM_IJKL ? plain_map(1, p0 * nq) : split_map(nq, 1, np_, p0);
+        OutDesc o2{T, plain_map(np_ * nq), ocol, 0};
+        if (c.mode == CC_FP64) {
+            GemmF64 g{};
+            g.M = o * o; g.N = (int)(Ab * nq); g.K = (int)vv;
+            g.A = t2; g.am = plain_map(vv); g.ak = plain_map(1);
+            g.B = V; g.bm = plain_map(vv); g.bk = plain_map(1);
+            g.out = o2;
+            CC_TRY(run_f64("term_kg2_f64", g, st));
+        } else {
+            if (c.mode == CC_OZAKI_BF16) {
+                // V[pl][q][c][d] = X * 2^(eA[(p0+pl) v + c] + eB[q v + d] + base)
+                FixedSrc fs{(const long long*)V, Ab * nq, vv, v, v, Aw.e, split_map(nq, v_, 0, p0 * v_), Bw.e,
+                            split_map(nq, 0, v_), kFixedBase};
+                CC_TRY(prep_fixed(c, fs, Vw, st));
+            } else {
+                RowSrc vs{V, plain_map(vv), plain_map(1), Ab * nq, vv};
+                CC_TRY(prep_rows(c, vs, Vw, st));
+            }
+            CC_TRY(run_tc("term_kg2_tc", c, o * o, (int)(Ab * nq), (int)vv, tw, 0, Vw, 0, o2, status, st));
+        }
+    }
+    return finish(status, flags, st);
+}
+
 // ----------------------------------------------------------------- adjoint
 // dt2 = forward with L'[P,a,c] = L[P,c,a] applied to W (integral symmetry (ac|bd)).
 // dL  = T1[W, t] + T1[W^swap, t^swap], T1[X,t][P,e,f] = sum_(b,d) L[P,b,d] M1[e,f,b,d],
@@ -1183,6 +1337,36 @@ int cc_ladder_gemm(int mode, int M, int N, int K, const double* A, int lda, cons
         CC_TRY(run_tc("gemm_tc", c, M, N, K, oa, 0, ob, 0, out, status, st));
     }
     return finish(status, 0, st);
+}
+
+int cc_ladder_term_workspace_size(int which, int o, int v, int n_chol, int mode, int slices, size_t budget_bytes,
+                                  size_t* bytes)
+{
+    if (!bytes) return CC_ERR_NULL;
+    TermCtx tc;
+    CC_TRY(term_ctx(which, o, v, n_chol, mode, slices, &tc));
+    size_t need = 0;
+    if (pick_term_block(tc, budget_bytes ? budget_bytes : kDefaultBudget, &need) < 0) return CC_ERR_BUDGET;
+    *bytes = need;
+    return CC_OK;
+}
+
+int cc_ladder_term(int which, int o, int v, int n_chol, const double* Lov, const double* Lvv, const double* t2,
+                   double* T, int mode, int flags, int slices, void* workspace, size_t ws_bytes, void* stream)
+{
+    return term_impl(which, o, v, n_chol, Lov, Lvv, t2, T, mode, flags, slices, workspace, ws_bytes, stream);
+}
+
+int cc_ladder_tijkl(int o, int v, int n_chol, const double* Lov, const double* t2, double* T, int mode,
+                    void* workspace, size_t ws_bytes, void* stream)
+{
+    return term_impl(CC_TERM_IJKL, o, v, n_chol, Lov, nullptr, t2, T, mode, 0, 0, workspace, ws_bytes, stream);
+}
+
+int cc_ladder_tijbk(int o, int v, int n_chol, const double* Lov, const double* Lvv, const double* t2, double* T,
+                    int mode, void* workspace, size_t ws_bytes, void* stream)
+{
+    return term_impl(CC_TERM_IJBK, o, v, n_chol, Lov, Lvv, t2, T, mode, 0, 0, workspace, ws_bytes, stream);
 }
 
 int cc_ladder_device_status(void* workspace, void* stream)

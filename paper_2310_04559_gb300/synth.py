@@ -61,6 +61,15 @@ def amplitudes(o: int, v: int, seed: int = 1, sigma: float = 1e-2, symmetric: bo
     return np.ascontiguousarray(x)
 
 
+def cholesky_ov(n: int, o: int, v: int, seed: int = 3, decay: float = 5.0,
+                rng: np.random.Generator | None = None) -> np.ndarray:
+    """Random occupied-virtual Cholesky block ``Lov[P, k, c]`` (n x o x v), vector P scaled by exp(-decay P / n)."""
+    rng = np.random.default_rng(seed) if rng is None else rng
+    x = rng.standard_normal((n, o, v))
+    x *= np.exp(-decay * np.arange(n, dtype=np.float64) / max(n, 1))[:, None, None]
+    return np.ascontiguousarray(x)
+
+
 def cotangent(o: int, v: int, seed: int = 2, rng: np.random.Generator | None = None) -> np.ndarray:
     """Random cotangent ``W[i, j, a, b] ~ N(0, 1)`` for ``loss = sum W * R``."""
     rng = np.random.default_rng(seed) if rng is None else rng

@@ -233,3 +233,64 @@ def test_gradient_adjoint_forms_and_entries(oracle):
     e1, e2 = oracle.ladder_grad_entries(L, t2, W, i1, i2)
     assert np.array_equal(e1, dt2.ravel()[i1]) or _rel(e1, dt2.ravel()[i1]) < 1e-15
     assert _rel(e2, dL.ravel()[i2]) < 1e-15
+
+
+# ------------------------------------------------- Eq. 8 and Eq. 9 (two-block terms)
+# tt_ijkl = sum_{P,c,d} L^P_kc L^P_ld t_ij^cd and tt_ijbk = sum_{P,c,d} L^P_bd L^P_kc t_ij^cd share
+# the ladder's contraction.  Pins: reduction to the pinned ladder when the occupied-virtual block is
+# part of the virtual-virtual one, rank-one closed forms that separate every index, the pair
+# symmetry of Eq. 8, and additivity over Cholesky batches.  A swapped output pair (k <-> l, b <-> k),
+# a c <-> d swap or an L_ck for L_kc fails at least one of them.
+
+def _terms_inputs(o, v, n, seed):
+    rng = np.random.default_rng(seed)
+    Lvv = synth.cholesky_vectors(n, v, symmetric=False, rng=rng)
+    Lov = synth.cholesky_ov(n, o, v, rng=rng)
+    t2 = synth.amplitudes(o, v, symmetric=False, rng=rng)
+    return Lov, Lvv, t2
+
+
+@pytest.mark.parametrize("o,v,n", [(2, 5, 3), (3, 7, 11), (4, 9, 6)])
+def test_terms_reduce_to_the_ladder(oracle, o, v, n):
+    """With Lov[P,k,c] = L[P,k,c] for k < o (o <= v), Eq. 8 is the ladder's R[i,j,k,l] and Eq. 9
+    is R[i,j,k,b] read as tt[i,j,b,k]."""
+    _, L, t2 = _terms_inputs(o, v, n, 40 + o)
+    R = oracle.ladder(L, t2)
+    Lov = np.ascontiguousarray(L[:, :o, :])
+    assert _rel(oracle.tijkl(Lov, t2), R[:, :, :o, :o]) < 1e-14
+    assert _rel(oracle.tijbk(Lov, L, t2), R[:, :, :o, :].transpose(0, 1, 3, 2)) < 1e-14
+
+
+def test_terms_rank_one_closed_forms(oracle):
+    """n = 1, Lov[0] = x y^T, Lvv[0] = u w^T:
+    tt_ijkl = x_k x_l (y^T t_ij y),  tt_ijbk = u_b x_k (y^T t_ij w)."""
+    o, v = 3, 6
+    rng = np.random.default_rng(44)
+    x, y = rng.standard_normal(o), rng.standard_normal(v)
+    u, w = rng.standard_normal(v), rng.standard_normal(v)
+    t2 = rng.standard_normal((o, o, v, v))
+    Lov = np.outer(x, y)[None]
+    Lvv = np.outer(u, w)[None]
+    s_yy = np.array([[y @ t2[i, j] @ y for j in range(o)] for i in range(o)])
+    s_yw = np.array([[y @ t2[i, j] @ w for j in range(o)] for i in range(o)])
+    ref1 = s_yy[:, :, None, None] * np.outer(x, x)[None, None]
+    ref2 = s_yw[:, :, None, None] * np.outer(u, x)[None, None]
+    assert _rel(oracle.tijkl(Lov, t2), ref1) < 1e-14
+    assert _rel(oracle.tijbk(Lov, Lvv, t2), ref2) < 1e-14
+
+
+def test_terms_pair_symmetry_and_batches(oracle):
+    """Eq. 8 inherits the pair symmetry: t_ijcd = t_jidc gives tt_ijkl = tt_jilk for any Lov.
+    Both terms are additive over concatenated Cholesky batches."""
+    o, v, n = 4, 8, 10
+    rng = np.random.default_rng(45)
+    Lov = synth.cholesky_ov(n, o, v, rng=rng)
+    Lvv = synth.cholesky_vectors(n, v, symmetric=False, rng=rng)
+    ts = synth.amplitudes(o, v, symmetric=True, rng=rng)
+    T = oracle.tijkl(Lov, ts)
+    assert _rel(T, T.transpose(1, 0, 3, 2)) < 1e-14
+    t2 = synth.amplitudes(o, v, symmetric=False, rng=rng)
+    for f in (lambda a, b: oracle.tijkl(a, t2), lambda a, b: oracle.tijbk(a, b, t2)):
+        whole = f(Lov, Lvv)
+        parts = f(Lov[:4], Lvv[:4]) + f(Lov[4:], Lvv[4:])
+        assert _rel(parts, whole) < 1e-13
