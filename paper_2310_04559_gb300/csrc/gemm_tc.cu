@@ -77,6 +77,7 @@ struct SmemCtl {
     unsigned int tmem_base;
     volatile int abort;
     long long rowoff[BM];
+    long long coloff[BN];   // -1 for columns beyond N
     int eA[BM];
     int eB[BN];
     float stage[EPI_WARPS][32][17];
@@ -364,6 +365,7 @@ gemm_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
     for (int c = threadIdx.x; c < BN; c += THREADS) {
         const int n = n0 + c;
         ctl->eB[c] = (p.eB && n < p.N) ? p.eB[p.rowB0 + n] : 0;
+        ctl->coloff[c] = (n < p.N) ? map2(p.out.cmap, n) : -1;
     }
     fence_before();
     __syncthreads();
@@ -579,9 +581,8 @@ gemm_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
             const uint32_t tl = tmem + ((uint32_t)row0 << 16);
             for (int sc = 0; sc < BN / 32; ++sc) {
                 const int col = half * (BN / 2) + sc * 16;  // tile column of the sub-chunk
-                const int n = n0 + col + cl;
-                const bool ncol = n < p.N;
-                const long long co = ncol ? map2(p.out.cmap, n) : 0;
+                const long long co = ctl->coloff[col + cl];
+                const bool ncol = co >= 0;
                 float a0[16], a1[16];
                 uint32_t r0[16], r1[16];
                 tmem_ld16(tl + (uint32_t)(buf0 * BN + col), r0);
