@@ -320,6 +320,21 @@ def run_ours(a):
             ms = h0.elapsed_time(h1)
             terms[name] = {"tflops": fl / (ms / 1e3) / 1e12, "ms": ms, "flops_algorithmic": fl}
         out["terms"] = terms
+        # host-resident amplitudes: t2 and R in page-locked host memory, read and written over the
+        # host link, the device holding L, one block of pairs and the integral blocks (20 GB budget)
+        Rh = torch.empty(t2_h.shape, dtype=torch.float64).pin_memory()
+        hb = 20 << 30
+        B.ladder_forward(Lg, t2_h, R=Rh, mode=mode, symmetric=True, host_t2r=True, budget=hb)
+        torch.cuda.synchronize(dev)
+        k0, k1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        k0.record(stream)
+        B.ladder_forward(Lg, t2_h, R=Rh, mode=mode, symmetric=True, host_t2r=True, budget=hb)
+        k1.record(stream)
+        torch.cuda.synchronize(dev)
+        hp = B.plan(o, v, n, mode=mode, symmetric=True, host_t2r=True, budget=hb)
+        out["host_resident"] = {"tflops": flops / (k0.elapsed_time(k1) / 1e3) / 1e12,
+                                "rel_err": rel(Rh.numpy()), "device_budget_gb": round(hb / 1e9, 1),
+                                "a_blocks": hp["n_blocks"], "ws_gb": round(hp["ws_bytes"] / 1e9, 2)}
         sample_flops = 2.0 * (o * o + n) * float(v) ** 3 * len(a_list)
         out["cpu_baseline"] = {"value": sample_flops / t_cpu / 1e12, "unit": UNIT, "cores": threads, "kind": "oracle",
                                "sample": f"R[:, :, a, :] for a in {a_list} of the same workload "

@@ -88,8 +88,15 @@ enum cc_flags {
                                    computes the pairs i <= j and mirrors them.                         */
     CC_FLAG_EXCHANGE = 4,       /* evaluate the exchange partner of Eq. 7 instead:
                                    R[i,j,a,b] = sum_cd (sum_P L_Pad L_Pbc) t2[i,j,c,d]                */
-    CC_FLAG_NO_STATUS_SYNC = 8  /* do not synchronise the stream at the end; device-side failures are
+    CC_FLAG_NO_STATUS_SYNC = 8, /* do not synchronise the stream at the end; device-side failures are
                                    then reported by cc_ladder_device_status()                         */
+    CC_FLAG_HOST_T2R = 16       /* t2 and R are page-locked HOST memory (cudaHostAlloc / cudaHostRegister,
+                                   addressable from the device); L, energy and the workspace stay on the
+                                   device.  The kernels read t2 and write R over the host link, so
+                                   o^2 v^2 may exceed device memory: the device holds one block of
+                                   pairs (i <= j) at a time.  Needs CC_FLAG_SYMMETRIC_T and the
+                                   integral-first order, not CC_FLAG_EXCHANGE (else CC_ERR_UNSUPPORTED);
+                                   CC_ERR_ARG if t2 or R is not page-locked host memory.              */
 };
 
 /* Full argument block for cc_ladder_fwd_ex / cc_ladder_workspace_size_ex. */
@@ -128,6 +135,8 @@ typedef struct cc_ladder_plan {
     size_t ws_bytes;       /* workspace the plan needs                           */
     double flops_algorithmic; /* 2(o^2+n)v^4 (integral-first) or 4 n o^2 v^3     */
     double flops_issued;      /* tensor-core flops actually issued (slice products, padding) */
+    int pair_blocks;          /* blocks of pairs (i <= j) the device holds one at a time (1 unless
+                                 CC_FLAG_HOST_T2R splits them to fit the workspace) */
 } cc_ladder_plan;
 
 /* Workspace bytes for cc_ladder_fwd with (mode, default order/flags) under `budget_bytes`

@@ -19,7 +19,7 @@ STATUS = {
 }
 MODES = {"fp64": 0, "ozaki_bf16": 1, "ozaki_int8": 2, "tf32": 3, "bf16": 4}
 ORDERS = {"auto": 0, "integral_first": 1, "cholesky_first": 2}
-FLAG_ACCUMULATE, FLAG_SYMMETRIC_T, FLAG_EXCHANGE, FLAG_NO_STATUS_SYNC = 1, 2, 4, 8
+FLAG_ACCUMULATE, FLAG_SYMMETRIC_T, FLAG_EXCHANGE, FLAG_NO_STATUS_SYNC, FLAG_HOST_T2R = 1, 2, 4, 8, 16
 
 _vp = ctypes.c_void_p
 _sz = ctypes.c_size_t
@@ -42,6 +42,7 @@ class Plan(ctypes.Structure):
     _fields_ = [
         ("order", _i), ("a_block", _i), ("n_blocks", _i), ("slices", _i), ("pairs", _i),
         ("ws_bytes", _sz), ("flops_algorithmic", ctypes.c_double), ("flops_issued", ctypes.c_double),
+        ("pair_blocks", _i),
     ]
 
 

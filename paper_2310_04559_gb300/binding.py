@@ -34,9 +34,10 @@ def _order(o) -> int:
     return _lib.ORDERS[o]
 
 
-def _flags(symmetric=False, exchange=False, accumulate=False, no_sync=False) -> int:
+def _flags(symmetric=False, exchange=False, accumulate=False, no_sync=False, host_t2r=False) -> int:
     return ((_lib.FLAG_SYMMETRIC_T if symmetric else 0) | (_lib.FLAG_EXCHANGE if exchange else 0)
-            | (_lib.FLAG_ACCUMULATE if accumulate else 0) | (_lib.FLAG_NO_STATUS_SYNC if no_sync else 0))
+            | (_lib.FLAG_ACCUMULATE if accumulate else 0) | (_lib.FLAG_NO_STATUS_SYNC if no_sync else 0)
+            | (_lib.FLAG_HOST_T2R if host_t2r else 0))
 
 
 def _check_tensor(x: torch.Tensor, name: str, shape):
@@ -67,14 +68,14 @@ def _shapes(L, t2):
 
 
 def make_args(o, v, n, mode="fp64", order="auto", symmetric=False, exchange=False, accumulate=False,
-              a_block=0, slices=0, budget=0, no_sync=False, a_range=None) -> _lib.Args:
+              a_block=0, slices=0, budget=0, no_sync=False, a_range=None, host_t2r=False) -> _lib.Args:
     a = _lib.Args()
     if a_range is not None:
         a.a_lo, a.a_hi = int(a_range[0]), int(a_range[1])
     a.o, a.v, a.n_chol = o, v, n
     a.mode, a.order = _mode(mode), _order(order)
     a.a_block, a.slices = int(a_block), int(slices)
-    a.flags = _flags(symmetric, exchange, accumulate, no_sync)
+    a.flags = _flags(symmetric, exchange, accumulate, no_sync, host_t2r)
     a.budget_bytes = int(budget)
     return a
 
@@ -96,7 +97,7 @@ def plan(o, v, n, ws_bytes=0, **kw) -> dict:
     _lib.check(lib.cc_ladder_plan_query(ctypes.byref(a), ctypes.byref(p)), "cc_ladder_plan_query")
     return {"order": {1: "integral_first", 2: "cholesky_first"}[p.order], "a_block": p.a_block,
             "n_blocks": p.n_blocks, "slices": p.slices, "pairs": p.pairs, "ws_bytes": p.ws_bytes,
-            "flops_algorithmic": p.flops_algorithmic, "flops_issued": p.flops_issued}
+            "flops_algorithmic": p.flops_algorithmic, "flops_issued": p.flops_issued, "pair_blocks": p.pair_blocks}
 
 
 def autotune(L, t2, R=None, mode="ozaki_bf16", symmetric=False, exchange=False, slices=0, budget=0,
@@ -129,19 +130,32 @@ def alloc_workspace(nbytes: int, device) -> torch.Tensor:
     return torch.empty(max(int(nbytes), 256), dtype=torch.uint8, device=device)
 
 
+def _check_host_tensor(x: torch.Tensor, name: str, shape):
+    if not isinstance(x, torch.Tensor) or x.device.type != "cpu" or not x.is_pinned():
+        raise ValueError(f"{name} must be a page-locked CPU tensor (tensor.pin_memory()) with host_t2r=True")
+    if x.dtype != torch.float64 or tuple(x.shape) != tuple(shape) or not x.is_contiguous():
+        raise ValueError(f"{name} must be contiguous float64 of shape {tuple(shape)}")
+
+
 def ladder_forward(L, t2, R=None, mode="ozaki_bf16", order="auto", symmetric=False, exchange=False,
                    accumulate=False, a_block=0, slices=0, energy=False, workspace=None, budget=0, no_sync=False,
-                   a_range=None):
+                   a_range=None, host_t2r=False):
     """R (new tensor unless given) and optionally the pair energy E (0-d tensor).
-    a_range=(lo, hi) computes only the columns a in [lo, hi) (see cc_ladder_args)."""
+    a_range=(lo, hi) computes only the columns a in [lo, hi) (see cc_ladder_args).
+    host_t2r=True: t2 and R are page-locked CPU tensors read and written over the host link
+    (problems whose o^2 v^2 exceeds device memory); needs symmetric=True."""
     lib = _lib.load()
     o, v, n = _shapes(L, t2)
     _check_tensor(L, "L", (n, v, v))
-    _check_tensor(t2, "t2", (o, o, v, v))
+    check = _check_host_tensor if host_t2r else _check_tensor
+    check(t2, "t2", (o, o, v, v))
     if R is None:
         R = torch.empty_like(t2) if not accumulate else torch.zeros_like(t2)
-    _check_tensor(R, "R", (o, o, v, v))
-    a = make_args(o, v, n, mode, order, symmetric, exchange, accumulate, a_block, slices, budget, no_sync, a_range)
+        if host_t2r:
+            R = R.pin_memory()
+    check(R, "R", (o, o, v, v))
+    a = make_args(o, v, n, mode, order, symmetric, exchange, accumulate, a_block, slices, budget, no_sync, a_range,
+                  host_t2r)
     if workspace is None:
         ws = ctypes.c_size_t()
         _lib.check(lib.cc_ladder_workspace_size_ex(ctypes.byref(a), ctypes.byref(ws)), "cc_ladder_workspace_size_ex")

@@ -78,6 +78,8 @@ struct Ctx {
     bool packed;      // pair-symmetric integral-first tensor-core path (R+ / R- over c <= d)
     long long pp, pm; // packed path: pairs i <= j and i < j
     long long Kp, Km; // packed path: v(v+1)/2 and v(v-1)/2
+    bool host;        // t2 and R are page-locked host memory, read and written over the host link
+    long long PB;     // packed path: pairs (i <= j) per pair block (o(o+1)/2 unless host)
 };
 
 // Blocks of `a` values [a0, a0 + Ab) covering [alo, ahi).  Unpacked paths: Ab = P
@@ -130,17 +132,18 @@ FwdLayout layout_packed(const Ctx& c, long long P)
         L.eL = cv.take(4 * vv);
         L.colmax = cv.take(8 * vv);
     }
-    L.Tp = cv.take(es * s * c.pp * pitch_for(c.Kp, es));
-    L.eTp = cv.take(4 * c.pp);
-    L.Tm = cv.take(es * s * c.pm * pitch_for(c.Km, es));
-    L.eTm = cv.take(4 * c.pm);
+    const long long pbm = std::min(c.PB, c.pm);  // pairs i < j in one pair block
+    L.Tp = cv.take(es * s * c.PB * pitch_for(c.Kp, es));
+    L.eTp = cv.take(4 * c.PB);
+    L.Tm = cv.take(es * s * pbm * pitch_for(c.Km, es));
+    L.eTm = cv.take(4 * pbm);
     L.rtab = cv.take(8 * P);
     L.Vp = cv.take(es * s * P * pitch_for(c.Kp, es));
     L.eVp = cv.take(4 * P);
     L.Vm = cv.take(es * s * P * pitch_for(c.Km, es));
     L.eVm = cv.take(4 * P);
-    L.Rpc = cv.take(8 * c.pp * P);
-    L.Rmc = cv.take(8 * c.pm * P);
+    L.Rpc = cv.take(8 * c.PB * P);
+    L.Rmc = cv.take(8 * pbm * P);
     L.total = cv.cur;
     return L;
 }
@@ -269,7 +272,25 @@ int pick_order(const Ctx& c, int requested)
 // Layout parameter fitting `bytes`: the block size A (unpacked paths: largest A, then
 // evened out over the blocks it implies), or the integral-row capacity P (packed path:
 // largest P in [v, v^2]; a requested a_block A means P = A v).  -1 if nothing fits.
-long long pick_block(const Ctx& c, size_t bytes, int requested, size_t* need)
+long long pick_block_pb(const Ctx& c, size_t bytes, int requested, size_t* need);
+
+// Host-resident t2 / R: the device holds one block of pairs at a time.  Pair blocks cost a new
+// split of their t2 rows for every integral block and shorter ladder GEMMs, so the largest pair
+// block (halving from all pairs) that still leaves room for integral blocks of at least 4 `a`
+// values (or all of them) is taken.
+long long pick_block(Ctx& c, size_t bytes, int requested, size_t* need)
+{
+    if (!(c.host && c.packed)) return pick_block_pb(c, bytes, requested, need);
+    const long long want = (long long)std::min(c.v, 4) * c.v;
+    for (long long pb = c.pp;; pb = (pb + 1) / 2) {
+        c.PB = pb;
+        const long long P = pick_block_pb(c, bytes, requested, need);
+        if (P >= 0 && (P >= want || requested > 0 || pb == 1)) return P;
+        if (pb == 1) return -1;
+    }
+}
+
+long long pick_block_pb(const Ctx& c, size_t bytes, int requested, size_t* need)
 {
     const long long unit = c.packed ? c.v : 1;
     if (requested > 0) {
@@ -302,7 +323,9 @@ int make_ctx(const cc_ladder_args* a, Ctx* c)
     if (a->mode < CC_FP64 || a->mode > CC_BF16) return CC_ERR_ARG;
     if (a->order < CC_ORDER_AUTO || a->order > CC_ORDER_CHOLESKY_FIRST) return CC_ERR_ARG;
     if (a->a_block < 0) return CC_ERR_ARG;
-    if (a->flags & ~(CC_FLAG_ACCUMULATE | CC_FLAG_SYMMETRIC_T | CC_FLAG_EXCHANGE | CC_FLAG_NO_STATUS_SYNC)) return CC_ERR_ARG;
+    if (a->flags & ~(CC_FLAG_ACCUMULATE | CC_FLAG_SYMMETRIC_T | CC_FLAG_EXCHANGE | CC_FLAG_NO_STATUS_SYNC |
+                     CC_FLAG_HOST_T2R))
+        return CC_ERR_ARG;
     if (a->mode == CC_OZAKI_BF16 && a->slices != 0 && (a->slices < 2 || a->slices > 8)) return CC_ERR_ARG;
     if (a->a_lo < 0 || a->a_hi < 0 || a->a_lo > a->v || a->a_hi > a->v || (a->a_hi && a->a_hi <= a->a_lo))
         return CC_ERR_ARG;
@@ -320,8 +343,14 @@ int make_ctx(const cc_ladder_args* a, Ctx* c)
     // the order's cost model sees the packed flop count
     const bool can_pack = c->sym;
     c->packed = can_pack;
-    c->order = pick_order(*c, a->order);
+    // host-resident amplitudes stream pair blocks through the integral-first order only
+    c->order = ((a->flags & CC_FLAG_HOST_T2R) && a->order == CC_ORDER_AUTO) ? (int)CC_ORDER_INTEGRAL_FIRST
+                                                                           : pick_order(*c, a->order);
     c->packed = can_pack && c->order == CC_ORDER_INTEGRAL_FIRST;
+    c->host = (a->flags & CC_FLAG_HOST_T2R) != 0;
+    c->PB = c->pp;
+    // host-resident amplitudes run on the packed path only, without the exchange copy
+    if (c->host && (!c->packed || c->exch)) return CC_ERR_UNSUPPORTED;
     return CC_OK;
 }
 
@@ -495,17 +524,34 @@ int fwd_packed(const Ctx& c, const cc_ladder_args* a, const double* Lsrc, const 
     Tm.D = at<void>(ws, Lo.Tm); Tm.e = at<int>(ws, Lo.eTm); Tm.rows = c.pm; Tm.pitch = pitch_for(c.Km, es);
     Vp.D = at<void>(ws, Lo.Vp); Vp.e = at<int>(ws, Lo.eVp); Vp.pitch = Tp.pitch;
     Vm.D = at<void>(ws, Lo.Vm); Vm.e = at<int>(ws, Lo.eVm); Vm.pitch = Tm.pitch;
-    {
-        if (!f64) {
-            // L rows (a,c) are contiguous in L[P][a][c]; K = P is strided
-            ColSrc ls{Lsrc, vv, vv, n, 0, plain_map(0)};
-            CC_TRY(prep_cols(c, ls, Lw, at<unsigned long long>(ws, Lo.colmax), st));
-        }
-        ProfScope ps("split", st);
-        CC_CU(pm_split_f64(t2, pairtab, 1, c.pp, c.v, +1, 1.0, kind, c.s, kBeta, Tp.D, Tp.pitch, Tp.e, st));
-        if (minus)
-            CC_CU(pm_split_f64(t2, pairtab_m, 1, c.pm, c.v, -1, 1.0, kind, c.s, kBeta, Tm.D, Tm.pitch, Tm.e, st));
+    if (!f64) {
+        // L rows (a,c) are contiguous in L[P][a][c]; K = P is strided
+        ColSrc ls{Lsrc, vv, vv, n, 0, plain_map(0)};
+        CC_TRY(prep_cols(c, ls, Lw, at<unsigned long long>(ws, Lo.colmax), st));
     }
+    // Pair blocks [q0, q1) of the i <= j pairs; their pairs i < j are [s0, s1) in the strict
+    // enumeration (s(p) = p - i - [j > i] pairs i < j precede pair p = (i, j)).
+    auto strict_before = [&](long long p) -> long long {
+        if (p >= c.pp) return c.pm;
+        long long i = 0, rem = p;
+        while (rem >= c.o - i) { rem -= c.o - i; ++i; }
+        return p - i - (rem > 0 ? 1 : 0);
+    };
+    std::vector<std::pair<long long, long long>> pblocks;
+    for (long long q0 = 0; q0 < c.pp; q0 += c.PB) pblocks.emplace_back(q0, std::min(c.pp, q0 + c.PB));
+    // T+ / T- of one pair block (t2 rows read where they are: device or page-locked host memory)
+    auto split_t = [&](long long q0, long long q1) -> int {
+        ProfScope ps("split", st);
+        const long long s0 = strict_before(q0), s1 = strict_before(q1);
+        Tp.rows = q1 - q0;
+        Tm.rows = s1 - s0;
+        CC_CU(pm_split_f64(t2, pairtab + q0, 1, q1 - q0, c.v, +1, 1.0, kind, c.s, kBeta, Tp.D, Tp.pitch, Tp.e, st));
+        if (minus && s1 > s0)
+            CC_CU(pm_split_f64(t2, pairtab_m + s0, 1, s1 - s0, c.v, -1, 1.0, kind, c.s, kBeta, Tm.D, Tm.pitch, Tm.e,
+                               st));
+        return CC_OK;
+    };
+    if (pblocks.size() == 1) CC_TRY(split_t(0, c.pp));
     double* V = at<double>(ws, Lo.V);
     double* Rpc = at<double>(ws, Lo.Rpc);
     double* Rmc = at<double>(ws, Lo.Rmc);
@@ -544,23 +590,29 @@ int fwd_packed(const Ctx& c, const cc_ladder_args* a, const double* Lsrc, const 
         }
         OutDesc op{Rpc, plain_map(nr), plain_map(1), 0};
         OutDesc om{Rmc, plain_map(nr), plain_map(1), 0};
-        if (f64) {
-            for (int sg = 0; sg < (minus ? 2 : 1); ++sg) {
-                const Operand& T = sg ? Tm : Tp;
-                const Operand& Vx = sg ? Vm : Vp;
-                GemmF64 g{};
-                g.M = (int)(sg ? c.pm : c.pp); g.N = (int)nr; g.K = (int)(sg ? c.Km : c.Kp);
-                g.A = (const double*)T.D; g.am = plain_map(T.pitch); g.ak = plain_map(1);
-                g.B = (const double*)Vx.D; g.bm = plain_map(Vx.pitch); g.bk = plain_map(1);
-                g.out = sg ? om : op;
-                CC_TRY(run_f64("kg2_f64", g, st));
+        for (const auto& pb : pblocks) {
+            const long long q0 = pb.first, q1 = pb.second;
+            const long long s0 = strict_before(q0), s1 = strict_before(q1);
+            if (pblocks.size() > 1) CC_TRY(split_t(q0, q1));
+            const bool mb = minus && s1 > s0;
+            if (f64) {
+                for (int sg = 0; sg < (mb ? 2 : 1); ++sg) {
+                    const Operand& T = sg ? Tm : Tp;
+                    const Operand& Vx = sg ? Vm : Vp;
+                    GemmF64 g{};
+                    g.M = (int)(sg ? s1 - s0 : q1 - q0); g.N = (int)nr; g.K = (int)(sg ? c.Km : c.Kp);
+                    g.A = (const double*)T.D; g.am = plain_map(T.pitch); g.ak = plain_map(1);
+                    g.B = (const double*)Vx.D; g.bm = plain_map(Vx.pitch); g.bk = plain_map(1);
+                    g.out = sg ? om : op;
+                    CC_TRY(run_f64("kg2_f64", g, st));
+                }
+            } else {
+                CC_TRY(run_tc("kg2_tc", c, (int)(q1 - q0), (int)nr, (int)c.Kp, Tp, 0, Vp, 0, op, status, st));
+                if (mb) CC_TRY(run_tc("kg2_tc", c, (int)(s1 - s0), (int)nr, (int)c.Km, Tm, 0, Vm, 0, om, status, st));
             }
-        } else {
-            CC_TRY(run_tc("kg2_tc", c, (int)c.pp, (int)nr, (int)c.Kp, Tp, 0, Vp, 0, op, status, st));
-            if (minus) CC_TRY(run_tc("kg2_tc", c, (int)c.pm, (int)nr, (int)c.Km, Tm, 0, Vm, 0, om, status, st));
+            ProfScope ps("scatter", st);
+            CC_CU(pm_combine(c.o, c.v, a0, Ab, Nb, nr, q0, q1, s0, Rpc, mb ? Rmc : nullptr, a->R, accum, st));
         }
-        ProfScope ps("scatter", st);
-        CC_CU(pm_combine(c.o, c.v, a0, Ab, Nb, nr, Rpc, minus ? Rmc : nullptr, a->R, accum, st));
     }
     return CC_OK;
 }
@@ -575,6 +627,17 @@ int fwd_impl(const cc_ladder_args* a, const double* Lsrc_override = nullptr)
         (a->energy && !aligned(a->energy, 8)))
         return CC_ERR_ALIGN;
     if (is_tc(c.mode) && !tc_gemm_available()) return CC_ERR_UNSUPPORTED;
+    if (c.host) {
+        // t2 and R must be page-locked host memory the device can address; L stays on the device
+        cudaPointerAttributes pa{};
+        for (const void* hp : {(const void*)a->t2, (const void*)a->R}) {
+            if (cudaPointerGetAttributes(&pa, hp) != cudaSuccess || pa.type != cudaMemoryTypeHost ||
+                pa.devicePointer != hp) {
+                cudaGetLastError();
+                return CC_ERR_ARG;
+            }
+        }
+    }
     size_t need = 0;
     const long long Pblk = pick_block(c, a->ws_bytes, a->a_block, &need);
     if (Pblk < 0) return CC_ERR_WORKSPACE;
@@ -1150,6 +1213,7 @@ int cc_ladder_plan_query(const cc_ladder_args* args, cc_ladder_plan* plan)
                                                      : 4.0 * c.n * (double)c.pairs * v * v * v) * frac;
     }
     plan->flops_issued = issued * nprod;
+    plan->pair_blocks = c.packed ? (int)((c.pp + c.PB - 1) / c.PB) : 1;
     return CC_OK;
 }
 

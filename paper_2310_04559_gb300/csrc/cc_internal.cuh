@@ -150,9 +150,10 @@ cudaError_t pm_split_fixed(const PmFixedSrc& src, int s, int beta, void* Dp, lon
 // rtab[rowbase(al) + b' - al] = al * Nb + b' for al < Ab, al <= b' < Nb (rowbase(al) = al Nb - al(al-1)/2)
 cudaError_t fill_rtab(int Ab, int Nb, long long* rtab, cudaStream_t st);
 // R[i,j,a,b], R[j,i,b,a] (=|+=) R+ + R-;  R[j,i,a,b], R[i,j,b,a] (=|+=) R+ - R-  for the block
-// a = a0 + al (al < Ab), b = a0 + b' (al <= b' < Nb); Rp[p][r] over pairs i <= j, Rm[q][r] over i < j.
-cudaError_t pm_combine(int o, int v, int a0, int Ab, int Nb, long long nr, const double* Rp, const double* Rm, double* R,
-                       int accumulate, cudaStream_t st);
+// a = a0 + al (al < Ab), b = a0 + b' (al <= b' < Nb) and the pairs q0 <= p < q1 (i <= j):
+// Rp[p - q0][r]; Rm[s(p) - s0][r] for their pairs i < j (s = index among the pairs i < j).
+cudaError_t pm_combine(int o, int v, int a0, int Ab, int Nb, long long nr, long long q0, long long q1, long long s0,
+                       const double* Rp, const double* Rm, double* R, int accumulate, cudaStream_t st);
 // tab = (i*o + j) * v*v for the pairs i < j (strict = 1) or i <= j (strict = 0), i-major
 cudaError_t fill_pairs(int o, int v, int strict, long long* tab, cudaStream_t st);
 // Plain fp64 -> tf32 (stored as fp32) copies, K-major.

@@ -312,22 +312,24 @@ __device__ __forceinline__ void pair_ij(int o, int p, int& i, int& j)
     j = ii + rem;
 }
 
-// R from R+ (rows: pairs i <= j) and R- (rows: pairs i < j) of one block; columns are
-// packed rows r (al, b' >= al).  Grid: x = pair p (i <= j), y = al.
-__global__ void pm_combine_kernel(int o, int v, int a0, int Nb, long long nr, const double* __restrict__ Rp,
-                                  const double* __restrict__ Rm, double* __restrict__ R, int accumulate)
+// R from R+ (rows: pairs q0 <= p < q1, i <= j) and R- (rows: their pairs i < j, from strict index
+// s0) of one block; columns are packed rows r (al, b' >= al).  Grid: x = pair p - q0, y = al.
+__global__ void pm_combine_kernel(int o, int v, int a0, int Nb, long long nr, long long q0, long long s0,
+                                  const double* __restrict__ Rp, const double* __restrict__ Rm,
+                                  double* __restrict__ R, int accumulate)
 {
-    const int p = blockIdx.x, al = blockIdx.y;
+    const long long pl = blockIdx.x;
+    const int p = (int)(q0 + pl), al = blockIdx.y;
     int i, j;
     pair_ij(o, p, i, j);
-    const int q = p - (i + 1);  // index among the pairs i < j
+    const long long q = p - (i + 1) - s0;  // row among this block's pairs i < j
     const long long vv = (long long)v * v;
     const long long base = (long long)al * Nb - (long long)al * (al - 1) / 2;
     const int a = a0 + al;
     double* Rij = R + ((long long)i * o + j) * vv;
     double* Rji = R + ((long long)j * o + i) * vv;
-    const double* rp = Rp + (long long)p * nr + base - al;
-    const double* rm = (i < j && Rm) ? Rm + (long long)q * nr + base - al : nullptr;
+    const double* rp = Rp + pl * nr + base - al;
+    const double* rm = (i < j && Rm) ? Rm + q * nr + base - al : nullptr;
     for (int bq = al + threadIdx.x; bq < Nb; bq += blockDim.x) {
         const int b = a0 + bq;
         const double plus = rp[bq];
@@ -392,13 +394,14 @@ cudaError_t fill_rtab(int Ab, int Nb, long long* rtab, cudaStream_t st)
     return cudaGetLastError();
 }
 
-cudaError_t pm_combine(int o, int v, int a0, int Ab, int Nb, long long nr, const double* Rp, const double* Rm, double* R,
-                       int accumulate, cudaStream_t st)
+cudaError_t pm_combine(int o, int v, int a0, int Ab, int Nb, long long nr, long long q0, long long q1, long long s0,
+                       const double* Rp, const double* Rm, double* R, int accumulate, cudaStream_t st)
 {
-    const long long np = (long long)o * (o + 1) / 2;
+    const long long np = q1 - q0;
     if (Ab <= 0 || np <= 0) return cudaSuccess;
-    if (Ab > 65535 || np > 0x7fffffffll) return cudaErrorInvalidValue;
-    pm_combine_kernel<<<dim3((unsigned)np, (unsigned)Ab), 256, 0, st>>>(o, v, a0, Nb, nr, Rp, Rm, R, accumulate);
+    if (Ab > 65535 || np > 0x7fffffffll || q0 < 0 || q1 > (long long)o * (o + 1) / 2) return cudaErrorInvalidValue;
+    pm_combine_kernel<<<dim3((unsigned)np, (unsigned)Ab), 256, 0, st>>>(o, v, a0, Nb, nr, q0, s0, Rp, Rm, R,
+                                                                        accumulate);
     count_launch();
     return cudaGetLastError();
 }
