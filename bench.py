@@ -320,10 +320,41 @@ def run_ours(a):
             ms = h0.elapsed_time(h1)
             terms[name] = {"tflops": fl / (ms / 1e3) / 1e12, "ms": ms, "flops_algorithmic": fl}
         out["terms"] = terms
+        # adjoint (dt2, dL of loss = <W, R>) on the o=16, v=160, n_chol=800 workload: forward and
+        # backward times, sampled gradient entries against the FP64 oracle
+        oa, va, na = 16, 160, 800
+        La_np, ta_np = synth.ladder_inputs(oa, va, na, seed=4)
+        Wa_np = synth.cotangent(oa, va, seed=5)
+        La, ta, Wa = (torch.from_numpy(x).to(dev) for x in (La_np, ta_np, Wa_np))
+        from oracle import oracle as O
+        gi = np.random.default_rng(6)
+        i1, i2 = gi.integers(0, ta_np.size, 16), gi.integers(0, La_np.size, 16)
+        e1, e2 = O.ladder_grad_entries(La_np, ta_np, Wa_np, i1, i2)
+        fwd_fl = algorithmic_flops(oa, va, na)
+        adj = {"workload": "o16_v160_n800", "flops_forward": fwd_fl, "flops_backward": 2 * fwd_fl}
+        for m in ("fp64", mode):
+            B.ladder_forward(La, ta, mode=m, symmetric=True)
+            dLa, dta = B.ladder_backward(La, ta, Wa, mode=m, symmetric=True)
+            torch.cuda.synchronize(dev)
+            a0_, a1_, a2_ = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+            a0_.record(stream)
+            B.ladder_forward(La, ta, mode=m, symmetric=True)
+            a1_.record(stream)
+            dLa, dta = B.ladder_backward(La, ta, Wa, mode=m, symmetric=True)
+            a2_.record(stream)
+            torch.cuda.synchronize(dev)
+            tf, tb = a0_.elapsed_time(a1_) / 1e3, a1_.elapsed_time(a2_) / 1e3
+            g1 = dta.cpu().numpy().ravel()[i1]
+            g2 = dLa.cpu().numpy().ravel()[i2]
+            adj[m] = {"forward_tflops": fwd_fl / tf / 1e12, "backward_tflops": 2 * fwd_fl / tb / 1e12,
+                      "backward_ms": tb * 1e3, "dt2_rel_err": float(np.linalg.norm(g1 - e1) / np.linalg.norm(e1)),
+                      "dL_rel_err": float(np.linalg.norm(g2 - e2) / np.linalg.norm(e2))}
+        out["adjoint"] = adj
+        del La, ta, Wa, dLa, dta
         # host-resident amplitudes: t2 and R in page-locked host memory, read and written over the
         # host link, the device holding L, one block of pairs and the integral blocks (20 GB budget)
         Rh = torch.empty(t2_h.shape, dtype=torch.float64).pin_memory()
-        hb = 20 << 30
+        hb = 40 << 30
         B.ladder_forward(Lg, t2_h, R=Rh, mode=mode, symmetric=True, host_t2r=True, budget=hb)
         torch.cuda.synchronize(dev)
         k0, k1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)

@@ -276,18 +276,23 @@ long long pick_block_pb(const Ctx& c, size_t bytes, int requested, size_t* need)
 
 // Host-resident t2 / R: the device holds one block of pairs at a time.  Pair blocks cost a new
 // split of their t2 rows for every integral block and shorter ladder GEMMs, so the largest pair
-// block (halving from all pairs) that still leaves room for integral blocks of at least 4 `a`
-// values (or all of them) is taken.
+// block (halving from all pairs) that leaves room for integral blocks of at least 4 `a` values
+// (or all of them) is taken; when no pair block does, the largest one that fits one `a` per block.
 long long pick_block(Ctx& c, size_t bytes, int requested, size_t* need)
 {
     if (!(c.host && c.packed)) return pick_block_pb(c, bytes, requested, need);
     const long long want = (long long)std::min(c.v, 4) * c.v;
+    long long fallback = -1;
     for (long long pb = c.pp;; pb = (pb + 1) / 2) {
         c.PB = pb;
         const long long P = pick_block_pb(c, bytes, requested, need);
-        if (P >= 0 && (P >= want || requested > 0 || pb == 1)) return P;
-        if (pb == 1) return -1;
+        if (P >= 0 && (P >= want || requested > 0)) return P;
+        if (P >= 0 && fallback < 0) fallback = pb;
+        if (pb == 1) break;
     }
+    if (fallback < 0) return -1;
+    c.PB = fallback;
+    return pick_block_pb(c, bytes, requested, need);
 }
 
 long long pick_block_pb(const Ctx& c, size_t bytes, int requested, size_t* need)

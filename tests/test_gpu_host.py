@@ -32,8 +32,8 @@ def pinned(x):
     return torch.from_numpy(np.ascontiguousarray(x)).pin_memory()
 
 
-@pytest.mark.parametrize("mode,budget,pblocks", [("ozaki_bf16", 0, 1), ("ozaki_bf16", 6 << 20, 45),
-                                                ("fp64", 0, 1), ("fp64", 4 << 20, 15), ("tf32", 3 << 20, 45)])
+@pytest.mark.parametrize("mode,budget,pblocks", [("ozaki_bf16", 0, 1), ("ozaki_bf16", 2700 << 10, 15),
+                                                ("fp64", 0, 1), ("fp64", 4100 << 10, 8), ("tf32", 3500 << 10, 23)])
 def test_host_resident_parity(dev, oracle, mode, budget, pblocks):
     o, v, n = 9, 40, 70
     plan = B.plan(o, v, n, mode=mode, symmetric=True, budget=budget, host_t2r=True)
