@@ -249,7 +249,9 @@ int cc_ladder_gemm(int mode, int M, int N, int K, const double* A, int lda, cons
  * those events and fills up to max_entries totals (phase name, launches, milliseconds,
  * tensor-core or FP64 flops issued); it returns the number of phases.  Profiling adds two
  * events per phase and is off by default.  cc_ladder_launch_count is the number of kernels
- * the library has launched in this process. */
+ * the library has launched in this process.  Every phase is also an NVTX range of the same name
+ * (visible in timeline profilers; free when none is attached), and with the environment variable
+ * CC_LADDER_VERBOSE set to a non-zero value every forward call prints its plan to stderr. */
 typedef struct cc_ladder_profile_entry {
     char name[32];
     int launches;

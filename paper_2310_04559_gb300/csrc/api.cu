@@ -648,6 +648,13 @@ int fwd_impl(const cc_ladder_args* a, const double* Lsrc_override = nullptr)
     if (Pblk < 0) return CC_ERR_WORKSPACE;
     const FwdLayout Lo = layout_fwd(c, Pblk);
     const int A = (int)Pblk;
+    if (const char* vb = getenv("CC_LADDER_VERBOSE")) {
+        if (*vb && *vb != '0')
+            fprintf(stderr, "cc_ladder: o=%d v=%d n=%d mode=%d order=%s packed=%d host=%d block-param=%lld "
+                            "pair-blocks=%lld workspace=%zu B of %zu\n",
+                    c.o, c.v, c.n, c.mode, c.order == CC_ORDER_INTEGRAL_FIRST ? "integral-first" : "cholesky-first",
+                    (int)c.packed, (int)c.host, Pblk, c.packed ? (c.pp + c.PB - 1) / c.PB : 1ll, need, a->ws_bytes);
+    }
     void* ws = a->workspace;
     cudaStream_t st = (cudaStream_t)a->stream;
     const long long o = c.o, v = c.v, n = c.n, vv = v * v;

@@ -1,8 +1,10 @@
 // profile.cu -- optional per-phase device timing (CUDA events on the caller's
 // stream) and a count of the library's kernel launches, for the benchmark and
 // for tracing.  Disabled by default; when disabled a ProfScope costs nothing but
-// a branch.
+// a branch and an NVTX range (every phase is an NVTX range named after it, which
+// timeline profilers show; without one attached the range calls do nothing).
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 
 #include <atomic>
 #include <cstring>
@@ -67,6 +69,7 @@ void count_launch(int n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
 
 ProfScope::ProfScope(const char* name, cudaStream_t s, double flops) : name_(name), s_(s), flops_(flops), e0_(nullptr)
 {
+    nvtxRangePushA(name);
     if (!g_enabled.load(std::memory_order_relaxed)) return;
     std::lock_guard<std::mutex> lk(g_mu);
     e0_ = get_event();
@@ -75,6 +78,7 @@ ProfScope::ProfScope(const char* name, cudaStream_t s, double flops) : name_(nam
 
 ProfScope::~ProfScope()
 {
+    nvtxRangePop();
     if (!e0_) return;
     std::lock_guard<std::mutex> lk(g_mu);
     cudaEvent_t e1 = get_event();
