@@ -378,8 +378,14 @@ cudaError_t pm_split_fixed(const PmFixedSrc& src, int s, int beta, void* Dp, lon
 {
     if (src.rows <= 0) return cudaSuccess;
     if (s < 1 || s > 8 || beta < 2 || beta > 9 || beta * s > 62 || src.v < 1) return cudaErrorInvalidValue;
+    // 8 v bytes of row / column exponents next to 17 KB of static tiles; above the 48 KB
+    // default the kernel opts in to the larger dynamic shared memory (v up to about 26000)
     const size_t smem = sizeof(int) * 2 * (size_t)src.v;
-    if (smem > 30 * 1024 || src.rows > 0x7fffffffll) return cudaErrorInvalidValue;
+    if (smem > 200 * 1024 || src.rows > 0x7fffffffll) return cudaErrorInvalidValue;
+    if (smem > 30 * 1024) {
+        const cudaError_t e = cudaFuncSetAttribute(pm_fixed_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+    }
     pm_fixed_kernel<<<(unsigned)src.rows, 256, smem, st>>>(src, s, beta, (__nv_bfloat16*)Dp, pitchp, ep,
                                                            (__nv_bfloat16*)Dm, pitchm, em);
     count_launch();

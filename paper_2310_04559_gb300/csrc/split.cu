@@ -318,7 +318,12 @@ cudaError_t split_fixed_rows_bf16(const FixedSrc& src, int s, int beta, void* D,
     if (src.rows <= 0) return cudaSuccess;
     if (s < 1 || s > 8 || beta < 2 || beta > 9 || beta * s > 62) return cudaErrorInvalidValue;
     const size_t smem = sizeof(int) * ((size_t)src.outer + src.inner);
-    if (smem > 48 * 1024) return cudaErrorInvalidValue;
+    if (smem > 200 * 1024) return cudaErrorInvalidValue;
+    if (smem > 48 * 1024) {  // opt in to the larger dynamic shared memory
+        const cudaError_t e =
+            cudaFuncSetAttribute(split_fixed_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+    }
     split_fixed_kernel<<<(unsigned)src.rows, 256, smem, st>>>(src, s, beta, (__nv_bfloat16*)D, pitch, e);
     count_launch();
     return cudaGetLastError();

@@ -123,3 +123,41 @@ def test_planner_orders(lib):
     assert Ld.plan(4, 96, 480, mode="ozaki_bf16", order="integral_first")["order"] == "integral_first"
     p = Ld.plan(60, 600, 3000, mode="ozaki_bf16", symmetric=True, budget=150 << 30)
     assert p["ws_bytes"] < 150 << 30 and p["pairs"] == 60 * 61 // 2 and p["slices"] == 6
+
+
+def test_host_resident_plans(lib):
+    """CC_FLAG_HOST_T2R: only the pair-symmetric integral-first path; the planner splits the pairs
+    into more blocks as the device budget shrinks, never below one `a` per integral block."""
+    from paper_2310_04559_gb300 import binding as Ld
+    with pytest.raises(_lib.LadderError) as e:
+        Ld.plan(9, 40, 70, mode="ozaki_bf16", symmetric=False, host_t2r=True, budget=1 << 30)
+    assert e.value.status == -6
+    with pytest.raises(_lib.LadderError) as e:
+        Ld.plan(9, 40, 70, mode="ozaki_bf16", symmetric=True, exchange=True, host_t2r=True, budget=1 << 30)
+    assert e.value.status == -6
+    last = 0
+    for kb in (64 << 10, 8 << 10, 4100, 3500, 2700):
+        p = Ld.plan(9, 40, 70, mode="ozaki_bf16", symmetric=True, host_t2r=True, budget=kb << 10)
+        assert p["order"] == "integral_first" and p["ws_bytes"] <= kb << 10
+        assert p["pair_blocks"] >= last and 1 <= p["a_block"] <= 40
+        last = p["pair_blocks"]
+    assert last > 1
+    # the work is the same however the pairs are blocked
+    full = Ld.plan(9, 40, 70, mode="ozaki_bf16", symmetric=True, budget=1 << 30)["flops_algorithmic"]
+    assert p["flops_algorithmic"] == full
+
+
+def test_term_workspace_queries(lib):
+    """Eq. 8 / Eq. 9 workspace queries: monotone in the budget, CC_ERR_BUDGET below the smallest
+    plan, CC_ERR_ARG for an unknown term."""
+    sizes = []
+    for b in (1 << 22, 1 << 26, 1 << 30):
+        out = ctypes.c_size_t()
+        st = lib.cc_ladder_term_workspace_size(2, 10, 64, 200, 1, 0, b, ctypes.byref(out))
+        sizes.append(out.value if st == 0 else 0)
+        assert st in (0, -5)
+    assert sizes == sorted(sizes) and sizes[-1] > 0
+    out = ctypes.c_size_t()
+    assert lib.cc_ladder_term_workspace_size(2, 10, 64, 200, 1, 0, 1 << 12, ctypes.byref(out)) == -5
+    assert lib.cc_ladder_term_workspace_size(3, 10, 64, 200, 1, 0, 1 << 30, ctypes.byref(out)) == -9
+    assert lib.cc_ladder_term(1, 2, 4, 4, None, None, None, None, 1, 0, 0, None, 0, None) == -2
