@@ -268,6 +268,17 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&r)[16])
 
 __device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
 
+// Fire-and-forget int64 store / add for the fixed-point epilogue: no result, no ordering with
+// other memory operations, so the 16 of a sub-chunk issue back to back.
+__device__ __forceinline__ void st_cg_s64(long long* p, long long x)
+{
+    asm volatile("st.global.cg.s64 [%0], %1;" ::"l"(p), "l"(x));
+}
+__device__ __forceinline__ void red_add_u64(long long* p, long long x)
+{
+    asm volatile("red.relaxed.gpu.global.add.u64 [%0], %1;" ::"l"(p), "l"(x));
+}
+
 __device__ __forceinline__ double pow2(int e)
 {
     e = e < -1022 ? -1022 : (e > 1023 ? 1023 : e);
@@ -552,6 +563,10 @@ gemm_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
         const int half = e >> 2;
         const int cl = lane & 15, rp = lane >> 4;
         float(*stg)[17] = ctl->stage[e];
+        // output row offsets of this lane's 16 rows (fixed for the CTA), kept in registers
+        long long ro_reg[16];
+#pragma unroll
+        for (int k = 0; k < 16; ++k) ro_reg[k] = ctl->rowoff[row0 + 2 * k + rp];
         uint32_t tuse0 = 0, tuse1 = 0;
         int toggle = 0;
         PassIter it;
@@ -615,13 +630,17 @@ gemm_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
                         // int64 result for a consumer that scales it: store (first pass of an
                         // unsplit tile), then add without reading
                         const bool store = first && p.epi == EPI_FIXED64_RED;
+                        if (ncol) {
+                            long long* cb = (long long*)(p.out.C + co);
+                            if (store) {
 #pragma unroll
-                        for (int k = 0; k < 16; ++k) {
-                            const long long ro = ctl->rowoff[row0 + 2 * k + rp];
-                            if (ro < 0 || !ncol) continue;
-                            unsigned long long* dst = (unsigned long long*)(p.out.C + ro + co);
-                            if (store) __stcg((long long*)dst, X[k]);
-                            else atomicAdd(dst, (unsigned long long)X[k]);
+                                for (int k = 0; k < 16; ++k)
+                                    if (ro_reg[k] >= 0) st_cg_s64(cb + ro_reg[k], X[k]);
+                            } else {
+#pragma unroll
+                                for (int k = 0; k < 16; ++k)
+                                    if (ro_reg[k] >= 0) red_add_u64(cb + ro_reg[k], X[k]);
+                            }
                         }
                         continue;
                     }
