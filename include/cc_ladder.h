@@ -103,8 +103,9 @@ enum cc_flags {
 typedef struct cc_ladder_args {
     int o, v, n_chol;      /* occupied, virtual, Cholesky-vector counts (>= 1)                */
     const double* L;       /* device [n_chol][v][v]                                             */
-    const double* t2;      /* device [o][o][v][v]                                               */
-    double* R;             /* device [o][o][v][v]; overwritten unless CC_FLAG_ACCUMULATE        */
+    const double* t2;      /* device [o][o][v][v] (page-locked host memory with CC_FLAG_HOST_T2R) */
+    double* R;             /* device [o][o][v][v] (host, as t2); overwritten unless
+                              CC_FLAG_ACCUMULATE                                                */
     double* energy;        /* nullable device scalar: E = sum_ijab (2 R_ijab - R_ijba) t2_ijab  */
     int mode;              /* cc_precision                                                      */
     int order;             /* cc_order                                                          */
@@ -119,16 +120,17 @@ typedef struct cc_ladder_args {
                               Entries written: R[i,j,a,b] for a in [a_lo, a_hi).  With
                               CC_FLAG_SYMMETRIC_T, integral-first: R[i,j,a,b] and R[i,j,b,a] for
                               all i, j, a in the range and b >= a; Cholesky-first: R[i,j,a,b]
-                              (i <= j) and R[j,i,b,a] (i < j) for a in the range.  Either way disjoint ranges write disjoint entries, so ranges
-                              spread over devices (each R zeroed first) assemble R by a sum.
-                              energy must be NULL unless the range is complete.                  */
+                              (i <= j) and R[j,i,b,a] (i < j) for a in the range.  Either way
+                              disjoint ranges write disjoint entries, so ranges spread over
+                              devices (each R zeroed first) assemble R by a sum.  energy must
+                              be NULL unless the range is complete.                              */
 } cc_ladder_args;
 
 /* What the planner decided for a call (for reporting and tests). */
 typedef struct cc_ladder_plan {
     int order;             /* CC_ORDER_INTEGRAL_FIRST or CC_ORDER_CHOLESKY_FIRST */
     int a_block;           /* `a` values in the first block                      */
-    int n_blocks;          /* number of blocks (pair-symmetric tensor-core plans widen their
+    int n_blocks;          /* number of blocks (pair-symmetric integral-first plans widen their
                               blocks as the b >= a range shrinks)                 */
     int slices;            /* Ozaki slices (1 for the non-emulated modes)        */
     int pairs;             /* GEMM rows used for (i,j): o*o, or o(o+1)/2 with symmetry */
