@@ -139,6 +139,24 @@ def oracle_sample(L, t2, a_list):
     return R, time.perf_counter() - t0, O.max_threads()
 
 
+def cpu_model() -> str:
+    """Host CPU model name (lscpu, else /proc/cpuinfo), for the CPU baseline record."""
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.strip().startswith("Model name:"):
+                return line.split(":", 1)[1].strip()
+    except (OSError, subprocess.SubprocessError):
+        pass
+    try:
+        for line in open("/proc/cpuinfo"):
+            if line.lower().startswith(("model name", "cpu part")):
+                return line.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    return "unknown"
+
+
 def traffic_record():
     """Per-launch DRAM bytes of the tensor-core GEMM from the committed ncu summary, if the
     kernel source is unchanged since it was captured (else None)."""
@@ -368,6 +386,7 @@ def run_ours(a):
                                 "a_blocks": hp["n_blocks"], "ws_gb": round(hp["ws_bytes"] / 1e9, 2)}
         sample_flops = 2.0 * (o * o + n) * float(v) ** 3 * len(a_list)
         out["cpu_baseline"] = {"value": sample_flops / t_cpu / 1e12, "unit": UNIT, "cores": threads, "kind": "oracle",
+                               "cpu_model": cpu_model(),
                                "sample": f"R[:, :, a, :] for a in {a_list} of the same workload "
                                          f"({len(a_list)}/{v} of the work, {t_cpu:.1f} s)"}
     if rank == 0:
@@ -401,7 +420,8 @@ def run_reference(a):
         "WORLD_SIZE", "1")), "steps": a.steps, "warmup": a.warmup, "ms_per_step": t_step * 1e3,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic", "config": {"workload": a.workload, "o": o, "v": v, "n_chol": n},
-        "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle", "sample": sample},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle", "sample": sample,
+                         "cpu_model": cpu_model()},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(out), flush=True)
 
