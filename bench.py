@@ -370,7 +370,7 @@ def run_ours(a):
         out["adjoint"] = adj
         del La, ta, Wa, dLa, dta
         # host-resident amplitudes: t2 and R in page-locked host memory, read and written over the
-        # host link, the device holding L, one block of pairs and the integral blocks (20 GB budget)
+        # host link, the device holding L, one block of pairs and the integral blocks (40 GB budget)
         Rh = torch.empty(t2_h.shape, dtype=torch.float64).pin_memory()
         hb = 40 << 30
         B.ladder_forward(Lg, t2_h, R=Rh, mode=mode, symmetric=True, host_t2r=True, budget=hb)

@@ -174,6 +174,32 @@ def test_workload_o20_v200_n1000_sampled(dev, oracle):
             assert rel(R, R.transpose(1, 0, 3, 2)) < 1e-15 + TOL[mode]
 
 
+def test_workload_o40_v400_n2000_sampled(dev, oracle):
+    """The o=40, v=400, n=2000 benchmark workload in the launch configuration the
+    benchmark times (emulated FP64, pair-symmetric packed path, workspace sized to a
+    150 GB device budget, no status sync in the call): sampled `a` columns against the
+    oracle, the pair symmetry of the whole R, and the pair energy against the oracle's
+    reduction of the same R within the rounding bound of an FP64 sum of 2.6e8 terms."""
+    o, v, n = 40, 400, 2000
+    L, t2 = synth.ladder_inputs(o, v, n, seed=0)
+    Lg, tg = cu(L, dev), cu(t2, dev)
+    budget = int(150e9) - L.nbytes - 2 * t2.nbytes - (2 << 30)
+    ws = B.alloc_workspace(B.workspace_size(o, v, n, mode="ozaki_bf16", symmetric=True, budget=budget), dev)
+    R = torch.empty_like(tg)
+    B.ladder_forward(Lg, tg, R=R, mode="ozaki_bf16", symmetric=True, workspace=ws, no_sync=True)
+    from paper_2310_04559_gb300 import _lib
+    _lib.check(_lib.load().cc_ladder_device_status(B._ptr(ws), B._stream(dev)), "o40 forward")
+    E = float(B.pair_energy(R, tg))
+    Rh = R.cpu().numpy()
+    del Lg, tg, R, ws
+    torch.cuda.empty_cache()
+    al = [0, 199, 399]
+    assert rel(Rh[:, :, al, :], oracle.ladder(L, t2, a_list=al)) < TOL["ozaki_bf16"]
+    assert rel(Rh, Rh.transpose(1, 0, 3, 2)) < 1e-15
+    terms = (2.0 * Rh - Rh.transpose(0, 1, 3, 2)) * t2
+    assert abs(E - oracle.energy(Rh, t2)) <= 1e-14 * float(np.abs(terms).sum())
+
+
 # ------------------------------------------------------------------ adjoint
 @pytest.mark.parametrize("mode", ["fp64", "ozaki_bf16"])
 def test_adjoint_vs_oracle(dev, oracle, mode):
