@@ -228,7 +228,7 @@ def test_adjoint_autograd_identities(dev):
     R = B.ladder(Lg, tg, mode="fp64", symmetric=True)
     loss = (R * cu(W, dev)).sum()
     loss.backward()
-    lv = float(loss)
+    lv = float(loss.detach())
     assert abs(float((tg.grad * tg).sum()) - lv) < 1e-11 * abs(lv)
     assert abs(float((Lg.grad * Lg).sum()) - 2 * lv) < 1e-11 * abs(lv)
 
