@@ -53,6 +53,13 @@ def _check_tensor(x: torch.Tensor, name: str, shape):
         raise ValueError(f"{name} must be contiguous")
 
 
+def _same_device(*xs):
+    """All CUDA tensors of one call live on one device (the stream is that device's)."""
+    devs = {x.device for x in xs if x is not None and x.device.type == "cuda"}
+    if len(devs) > 1:
+        raise ValueError(f"tensors on different devices: {sorted(str(d) for d in devs)}")
+
+
 def _ptr(x):
     return ctypes.c_void_p(x.data_ptr()) if x is not None else None
 
@@ -160,6 +167,7 @@ def ladder_forward(L, t2, R=None, mode="ozaki_bf16", order="auto", symmetric=Fal
         ws = ctypes.c_size_t()
         _lib.check(lib.cc_ladder_workspace_size_ex(ctypes.byref(a), ctypes.byref(ws)), "cc_ladder_workspace_size_ex")
         workspace = alloc_workspace(ws.value, L.device)
+    _same_device(L, t2, R, workspace)
     E = torch.empty((), dtype=torch.float64, device=L.device) if energy else None
     a.L, a.t2, a.R, a.energy = _ptr(L), _ptr(t2), _ptr(R), _ptr(E)
     a.workspace, a.ws_bytes = _ptr(workspace), workspace.numel()
@@ -176,6 +184,7 @@ def ladder_backward(L, t2, dR, mode="ozaki_bf16", symmetric=False, want_dL=True,
     _check_tensor(L, "L", (n, v, v))
     _check_tensor(t2, "t2", (o, o, v, v))
     _check_tensor(dR, "dR", (o, o, v, v))
+    _same_device(L, t2, dR, workspace)
     if workspace is None:
         ws = ctypes.c_size_t()
         _lib.check(lib.cc_ladder_bwd_workspace_size(o, v, n, _mode(mode), int(budget), ctypes.byref(ws)),
@@ -205,6 +214,7 @@ def term(which, Lov, t2, Lvv=None, mode="ozaki_bf16", slices=0, budget=0, T=None
     if T is None:
         T = torch.empty(shape, dtype=torch.float64, device=Lov.device)
     _check_tensor(T, "T", shape)
+    _same_device(Lov, Lvv, t2, T, workspace)
     if workspace is None:
         ws = ctypes.c_size_t()
         _lib.check(lib.cc_ladder_term_workspace_size(w, o, v, n, _mode(mode), int(slices), int(budget),
@@ -233,6 +243,7 @@ def pair_energy(R, t2, pairs=False):
     o, v = t2.shape[0], t2.shape[2]
     _check_tensor(R, "R", (o, o, v, v))
     _check_tensor(t2, "t2", (o, o, v, v))
+    _same_device(R, t2)
     ws = ctypes.c_size_t()
     _lib.check(lib.cc_ladder_energy_workspace_size(o, v, ctypes.byref(ws)), "cc_ladder_energy_workspace_size")
     w = alloc_workspace(ws.value, R.device)
@@ -253,6 +264,7 @@ def gemm(A, B, mode="ozaki_bf16", C=None, accumulate=False, slices=0):
     if C is None:
         C = torch.zeros((M, N), dtype=torch.float64, device=A.device)
     _check_tensor(C, "C", (M, N))
+    _same_device(A, B, C)
     ws = ctypes.c_size_t()
     _lib.check(lib.cc_ladder_gemm_workspace_size(_mode(mode), M, N, K, int(slices), ctypes.byref(ws)),
                "cc_ladder_gemm_workspace_size")

@@ -161,3 +161,27 @@ def test_term_workspace_queries(lib):
     assert lib.cc_ladder_term_workspace_size(2, 10, 64, 200, 1, 0, 1 << 12, ctypes.byref(out)) == -5
     assert lib.cc_ladder_term_workspace_size(3, 10, 64, 200, 1, 0, 1 << 30, ctypes.byref(out)) == -9
     assert lib.cc_ladder_term(1, 2, 4, 4, None, None, None, None, 1, 0, 0, None, 0, None) == -2
+
+
+def test_binding_refuses_cpu_tensors(lib):
+    """The product path has no CPU fallback: CPU tensors, wrong dtypes, shapes and layouts are
+    refused before anything reaches the library."""
+    import torch
+
+    from paper_2310_04559_gb300 import binding as Ld
+    o, v, n = 2, 5, 3
+    L = torch.zeros((n, v, v), dtype=torch.float64)
+    t2 = torch.zeros((o, o, v, v), dtype=torch.float64)
+    calls = [lambda: Ld.ladder_forward(L, t2), lambda: Ld.ladder_backward(L, t2, t2),
+             lambda: Ld.pair_energy(t2, t2), lambda: Ld.gemm(L[0], L[0]),
+             lambda: Ld.tijkl(torch.zeros((n, o, v), dtype=torch.float64), t2),
+             lambda: Ld.ladder(L, t2)]
+    for call in calls:
+        with pytest.raises(ValueError, match="CUDA tensor"):
+            call()
+    with pytest.raises(ValueError, match="page-locked"):
+        Ld._check_host_tensor(t2, "t2", (o, o, v, v))  # host_t2r=True wants pinned t2 and R
+    with pytest.raises(ValueError, match="unknown mode"):
+        Ld.workspace_size(o, v, n, mode="fp16")
+    with pytest.raises(ValueError, match="unknown order"):
+        Ld.plan(o, v, n, order="sideways")
