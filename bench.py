@@ -338,6 +338,36 @@ def run_ours(a):
             ms = h0.elapsed_time(h1)
             terms[name] = {"tflops": fl / (ms / 1e3) / 1e12, "ms": ms, "flops_algorithmic": fl}
         out["terms"] = terms
+        # both contraction orders (Section 3.2), each timed after a warm-up call and counted
+        # against its own algorithmic flops (2(o^2+n)v^4 integral-first, 4 n o^2 v^3
+        # Cholesky-first), next to the order the autotuner picks for the shape
+        orders = {}
+        for (oo, vo, no), bud in (((4, 96, 480), 8 << 30), ((20, 200, 1000), 24 << 30)):
+            key = f"o{oo}_v{vo}_n{no}"
+            try:
+                Lo_np, to_np = synth.ladder_inputs(oo, vo, no, seed=21)
+                Lo, to = torch.from_numpy(Lo_np).to(dev), torch.from_numpy(to_np).to(dev)
+                Ro = torch.empty_like(to)
+                rec = {}
+                for od, fl in (("integral_first", 2.0 * (oo * oo + no) * float(vo) ** 4),
+                               ("cholesky_first", 4.0 * no * oo * oo * float(vo) ** 3)):
+                    wso = B.alloc_workspace(B.workspace_size(oo, vo, no, mode=mode, order=od, symmetric=True,
+                                                             budget=bud), dev)
+                    B.ladder_forward(Lo, to, R=Ro, mode=mode, order=od, symmetric=True, workspace=wso)
+                    q0, q1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                    q0.record(stream)
+                    B.ladder_forward(Lo, to, R=Ro, mode=mode, order=od, symmetric=True, workspace=wso)
+                    q1.record(stream)
+                    torch.cuda.synchronize(dev)
+                    ms = q0.elapsed_time(q1)
+                    rec[od] = {"ms": ms, "tflops": fl / (ms / 1e3) / 1e12, "flops_algorithmic": fl}
+                    del wso
+                rec["autotuner_choice"] = B.autotune(Lo, to, R=Ro, mode=mode, symmetric=True, budget=bud)["order"]
+                orders[key] = rec
+                del Lo, to, Ro
+            except Exception as e:  # noqa: BLE001 - reported in the JSON line, the main figures stand
+                orders[key] = {"error": f"{type(e).__name__}: {e}"}
+        out["orders"] = orders
         # adjoint (dt2, dL of loss = <W, R>) on the o=16, v=160, n_chol=800 workload: forward and
         # backward times, sampled gradient entries against the FP64 oracle
         oa, va, na = 16, 160, 800
