@@ -63,7 +63,11 @@ enum cc_status {
 enum cc_precision {
     CC_FP64 = 0,       /* FP64 tensor-core MMA (DMMA), FP64 accumulation              */
     CC_OZAKI_BF16 = 1, /* FP64 emulated by split BF16 integer slices (Ozaki scheme) on
-                          tcgen05 tensor cores, exact FP32 slice products, FP64 recombination */
+                          tcgen05 tensor cores, FP32 accumulation of each slice-product level,
+                          exact int64 / FP64 recombination.  A level's FP32 sum is exact while its
+                          partial sums stay below 2^24: for any input when the contraction length
+                          is at most 4096 / (level + 1), and for all but adversarially aligned
+                          inputs beyond that (row-max scaling keeps typical sums near 2^17..2^21) */
     CC_OZAKI_INT8 = 2, /* INT8-slice emulation: tcgen05 has no kind::i8 on sm_103a;
                           always returns CC_ERR_UNSUPPORTED                           */
     CC_TF32 = 3,       /* TF32 inputs, FP32 accumulation per K-chunk, FP64 across chunks */
