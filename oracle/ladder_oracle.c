@@ -151,6 +151,44 @@ void oracle_ladder(int o, int v, int n, const double* L, const double* t2, doubl
 }
 
 /*
+ * Selected entries R[i,j,a,b] of Eq. 6, one by one, for spot checks of workloads whose full
+ * oracle would take hours.  idx[k] = ((i*o + j)*v + a)*v + b.  Each entry builds its own
+ * slice (ac|bd) over all (c, d) (Eq. 5, P in increasing order) and contracts it with t_ij
+ * (c then d), the same sums in the same order as oracle_ladder's entry.
+ */
+void oracle_ladder_entries(int o, int v, int n, const double* L, const double* t2, const long long* idx,
+                           int nidx, double* out, int nthreads)
+{
+    set_threads(nthreads);
+    const size_t vv = (size_t)v * v;
+#pragma omp parallel
+    {
+        double* Vab = (double*)malloc(sizeof(double) * vv);
+#pragma omp for schedule(dynamic, 1)
+        for (int k = 0; k < nidx; ++k) {
+            long long q = idx[k];
+            const int b = (int)(q % v); q /= v;
+            const int a = (int)(q % v); q /= v;
+            const int j = (int)(q % o); q /= o;
+            const int i = (int)q;
+            for (size_t e = 0; e < vv; ++e) Vab[e] = 0.0;
+            for (int P = 0; P < n; ++P) {
+                const double* La = L + (size_t)P * vv + (size_t)a * v;
+                const double* Lb = L + (size_t)P * vv + (size_t)b * v;
+                for (int c = 0; c < v; ++c)
+                    for (int d = 0; d < v; ++d) Vab[(size_t)c * v + d] += La[c] * Lb[d];
+            }
+            const double* tij = t2 + ((size_t)i * o + j) * vv;
+            double r = 0.0;
+            for (int c = 0; c < v; ++c)
+                for (int d = 0; d < v; ++d) r += Vab[(size_t)c * v + d] * tij[(size_t)c * v + d];
+            out[k] = r;
+        }
+        free(Vab);
+    }
+}
+
+/*
  * Brute force for tiny inputs, the integral-first path of Section 3.2: build
  * the whole dense integral tensor ERI[a][c][b][d] = sum_P L_Pac L_Pbd
  * (Eq. 5, v^4 doubles), then contract it with t over (c, d) (Eq. 4).

@@ -10,6 +10,7 @@ Functions (each follows the passage cited in ladder_oracle.c):
 * ``ladder(L, t2, a_list=None, compensated=False)`` -- Eq. 5 + Eq. 6 through the
   for-loop over ``a`` of Section 3.2.
 * ``ladder_eri(L, t2)`` -- brute force through the dense integral tensor (Eq. 4/5).
+* ``ladder_entries(L, t2, idx)`` -- selected entries of Eq. 6, one by one.
 * ``energy(R, t2)`` -- E = sum (2 R_ijab - R_ijba) t_ijab.
 * ``ladder_grad(L, t2, W)`` -- dt2, dL of loss = <W, R>.
 * ``ladder_grad_entries(...)`` -- selected gradient entries.
@@ -52,6 +53,8 @@ def _load():
         lib.oracle_ladder.argtypes = [ctypes.c_int] * 3 + [_dp, _dp, _dp, ctypes.POINTER(ctypes.c_int),
                                                            ctypes.c_int, ctypes.c_int, ctypes.c_int]
         lib.oracle_ladder_eri.argtypes = [ctypes.c_int] * 3 + [_dp, _dp, _dp, _dp]
+        lib.oracle_ladder_entries.argtypes = [ctypes.c_int] * 3 + [_dp, _dp, ctypes.POINTER(ctypes.c_longlong),
+                                                                   ctypes.c_int, _dp, ctypes.c_int]
         lib.oracle_energy.argtypes = [ctypes.c_int, ctypes.c_int, _dp, _dp, _dp]
         lib.oracle_energy.restype = ctypes.c_double
         lib.oracle_ladder_grad.argtypes = [ctypes.c_int] * 3 + [_dp, _dp, _dp, _dp, _dp, ctypes.c_int]
@@ -110,6 +113,19 @@ def ladder_eri(L, t2):
     eri = np.empty((v, v, v, v))
     lib.oracle_ladder_eri(o, v, n, _p(L), _p(t2), _p(R), _p(eri))
     return R
+
+
+def ladder_entries(L, t2, idx, threads=0):
+    """R.ravel()[idx] for flat indices into o*o*v*v, each computed on its own."""
+    lib = _load()
+    L, t2 = _f64(L), _f64(t2)
+    o, v, n = _shapes(L, t2)
+    ii = np.ascontiguousarray(idx, dtype=np.int64)
+    assert ii.size == 0 or (ii.min() >= 0 and ii.max() < o * o * v * v)
+    out = np.empty(ii.size)
+    lib.oracle_ladder_entries(o, v, n, _p(L), _p(t2), ii.ctypes.data_as(ctypes.POINTER(ctypes.c_longlong)),
+                              ii.size, _p(out), threads)
+    return out
 
 
 def energy(R, t2, pair=False):

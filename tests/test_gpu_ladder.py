@@ -200,6 +200,34 @@ def test_workload_o40_v400_n2000_sampled(dev, oracle):
     assert abs(E - oracle.energy(Rh, t2)) <= 1e-14 * float(np.abs(terms).sum())
 
 
+def test_workload_o60_v600_n3000_sampled_entries(dev, oracle):
+    """The largest workload (o=60, v=600, n=3000: 15 blocks of `a` under a 150 GB device
+    budget) in emulated FP64 with pair symmetry: 32 entries R[i,j,a,b] against the oracle's
+    entries computed one by one (the full oracle would take hours), scaled by the norm of the
+    sampled oracle values, and R[i,j,a,b] = R[j,i,b,a] at the same places."""
+    o, v, n = 60, 600, 3000
+    L, t2 = synth.ladder_inputs(o, v, n, seed=0)
+    Lg, tg = cu(L, dev), cu(t2, dev)
+    budget = int(150e9) - L.nbytes - 2 * t2.nbytes - (2 << 30)
+    ws = B.alloc_workspace(B.workspace_size(o, v, n, mode="ozaki_bf16", symmetric=True, budget=budget), dev)
+    R = torch.empty_like(tg)
+    B.ladder_forward(Lg, tg, R=R, mode="ozaki_bf16", symmetric=True, workspace=ws)
+    rng = np.random.default_rng(60)
+    i, j, a, b = (rng.integers(0, m, 32) for m in (o, o, v, v))
+    # include the corners and the diagonal cases of the four-way write
+    i[:4], j[:4], a[:4], b[:4] = [0, o - 1, 5, 7], [0, o - 1, 5, 9], [0, v - 1, 11, 13], [0, v - 1, 11, 2]
+    idx = ((i * o + j) * v + a) * v + b
+    mirror = ((j * o + i) * v + b) * v + a
+    flat = R.view(-1)
+    got = flat[torch.from_numpy(idx).to(dev)].cpu().numpy()
+    got_m = flat[torch.from_numpy(mirror).to(dev)].cpu().numpy()
+    del Lg, tg, R, ws, flat
+    torch.cuda.empty_cache()
+    ref = oracle.ladder_entries(L, t2, idx)
+    assert rel(got, ref) < TOL["ozaki_bf16"]
+    assert np.array_equal(got, got_m)
+
+
 # ------------------------------------------------------------------ adjoint
 @pytest.mark.parametrize("mode", ["fp64", "ozaki_bf16"])
 def test_adjoint_vs_oracle(dev, oracle, mode):

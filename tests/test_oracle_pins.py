@@ -167,6 +167,21 @@ def test_a_list_sampling_and_compensation(oracle):
     assert _rel(R, Rc) < 1e-14
 
 
+def test_entries_match_the_full_term(oracle):
+    """Entries computed one by one are the full term's entries bit for bit (same sums in the
+    same order) and agree with the brute force through the dense integral tensor; a transposed
+    L (non-symmetric here) or a swapped (a, b) would fail."""
+    o, v, n = 3, 11, 9
+    rng = np.random.default_rng(24)
+    L = synth.cholesky_vectors(n, v, symmetric=False, rng=rng)
+    t2 = synth.amplitudes(o, v, symmetric=False, rng=rng)
+    R = oracle.ladder(L, t2)
+    idx = np.concatenate([rng.integers(0, R.size, 40), [0, R.size - 1]])
+    assert np.array_equal(oracle.ladder_entries(L, t2, idx), R.ravel()[idx])
+    assert _rel(oracle.ladder_entries(L, t2, idx), oracle.ladder_eri(L, t2).ravel()[idx]) < 1e-14
+    assert oracle.ladder_entries(L, t2, []).size == 0
+
+
 # ----------------------------------------------------------------- energy
 def test_energy_hand_and_identities(oracle):
     # o = v = 1: E = (2R - R) t = R t = (sum_P L_P^2) t^2
