@@ -22,7 +22,7 @@ from __future__ import annotations
 
 import numpy as np
 
-__all__ = ["cholesky_vectors", "amplitudes", "cotangent", "ladder_inputs", "WORKLOADS"]
+__all__ = ["cholesky_vectors", "amplitudes", "cholesky_ov", "cotangent", "ladder_inputs", "WORKLOADS"]
 
 # Named workloads (o occupied, v virtual, n Cholesky vectors).  The paper's
 # synthetic shapes (Section 6.2, Table 1) use n = 5K, v = int(3K/4), o = K - v;
