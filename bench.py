@@ -29,7 +29,10 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 WORKLOADS = {"o40_v400_n2000": (40, 400, 2000), "o20_v200_n1000": (20, 200, 1000),
-             "o60_v600_n3000": (60, 600, 3000), "o16_v160_n800": (16, 160, 800), "o4_v24_n60": (4, 24, 60)}
+             "o60_v600_n3000": (60, 600, 3000), "o16_v160_n800": (16, 160, 800), "o4_v24_n60": (4, 24, 60),
+             # the paper's synthetic shapes of Table 1: n = 5K, v = 3K/4, o = K - v for K = 300, 400, 500
+             "o75_v225_n1500": (75, 225, 1500), "o100_v300_n2000": (100, 300, 2000),
+             "o125_v375_n2500": (125, 375, 2500)}
 METRIC = "ladder-term TFLOP/s (emulated FP64)"
 UNIT = "TFLOP/s"
 
