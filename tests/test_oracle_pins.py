@@ -29,6 +29,17 @@ def _rel(a, b):
 
 
 # ---------------------------------------------------------------- golden case
+def test_golden_terms_hand_computed(oracle):
+    """Eq. 7, Eq. 8 and Eq. 9 on a hand-computed case (derivation in the fixture)."""
+    g = json.load(open(os.path.join(GOLDEN, "terms_o1_v2_n2.json")))
+    L = np.array(g["L"], dtype=float)
+    t2 = np.array(g["t2"], dtype=float)
+    Lov = np.array(g["Lov"], dtype=float)
+    assert np.array_equal(oracle.exchange(L, t2), np.array(g["X"], dtype=float))
+    assert np.array_equal(oracle.tijkl(Lov, t2), np.array(g["tijkl"], dtype=float))
+    assert np.array_equal(oracle.tijbk(Lov, L, t2), np.array(g["tijbk"], dtype=float))
+
+
 def test_golden_hand_computed(oracle):
     g = json.load(open(os.path.join(GOLDEN, "ladder_o1_v2_n2.json")))
     L = np.array(g["L"], dtype=float)
