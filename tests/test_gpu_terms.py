@@ -73,3 +73,24 @@ def test_terms_reduce_to_ladder_on_device(dev):
     T2 = B.tijbk(Lov, Lg, tg, mode="ozaki_bf16").cpu().numpy()
     assert rel(T1, R[:, :, :o, :o]) < 1e-10
     assert rel(T2, R[:, :, :o, :].transpose(0, 1, 3, 2)) < 1e-10
+
+
+@pytest.mark.parametrize("mode", list(TOL))
+def test_golden_cases_on_device(dev, oracle, mode):
+    """The hand-computed o = 1, v = 2, n = 2 cases (ladder, energy, exchange, Eq. 8, Eq. 9) through
+    the C ABI: small integers, so every mode should reproduce them to its tolerance or better."""
+    import json
+    import os
+    gdir = os.path.join(os.path.dirname(__file__), "golden")
+    g1 = json.load(open(os.path.join(gdir, "ladder_o1_v2_n2.json")))
+    g2 = json.load(open(os.path.join(gdir, "terms_o1_v2_n2.json")))
+    L, t2, Lov = (np.array(g2[k], dtype=float) for k in ("L", "t2", "Lov"))
+    R, E = B.ladder_forward(cu(L, dev), cu(t2, dev), mode=mode, energy=True)
+    assert rel(R.cpu().numpy(), np.array(g1["R"], dtype=float)) < TOL[mode]
+    assert abs(float(E) - g1["E"]) <= TOL[mode] * abs(g1["E"])
+    X = B.ladder_forward(cu(L, dev), cu(t2, dev), mode=mode, exchange=True).cpu().numpy()
+    assert rel(X, np.array(g2["X"], dtype=float)) < TOL[mode]
+    T1 = B.tijkl(cu(Lov, dev), cu(t2, dev), mode=mode).cpu().numpy()
+    assert rel(T1, np.array(g2["tijkl"], dtype=float)) < TOL[mode]
+    T2 = B.tijbk(cu(Lov, dev), cu(L, dev), cu(t2, dev), mode=mode).cpu().numpy()
+    assert rel(T2, np.array(g2["tijbk"], dtype=float)) < TOL[mode]
