@@ -68,9 +68,9 @@ enum cc_precision {
                           partial sums stay below 2^24: for any input when the contraction length
                           is at most 4096 / (level + 1), and for all but adversarially aligned
                           inputs beyond that (row-max scaling keeps typical sums near 2^17..2^22).
-                          Exception: the diagonal integrals (ac|ac) of the integral build stay
-                          exact up to n_chol of about 12 000 only; beyond it they carry a few
-                          1e-10 relative error. */
+                          The integral builds split contractions longer than 6144 across CTAs
+                          with exact int64 partial sums, so their diagonal integrals (ac|ac), whose
+                          lower-digit squares add with one sign, stay exact for any n_chol. */
     CC_OZAKI_INT8 = 2, /* INT8-slice emulation: tcgen05 has no kind::i8 on sm_103a;
                           always returns CC_ERR_UNSUPPORTED                           */
     CC_TF32 = 3,       /* TF32 inputs, FP32 accumulation per K-chunk, FP64 across chunks */

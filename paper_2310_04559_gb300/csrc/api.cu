@@ -48,6 +48,12 @@ constexpr int kDefaultSlices = 6;
 constexpr int kBeta = 7;                 // bits per Ozaki slice (balanced digits in [-64, 64])
 constexpr int kMixedChunk = 16384;       // K elements per FP32 accumulation in the BF16 / TF32 modes
 constexpr int kFixF = 26;                // fixed-point fraction bits (of a level-0 unit) in the Ozaki epilogue
+// Longest contraction one FP32 level sum covers in an integral build (A and B rows from the same
+// Cholesky vectors).  In a diagonal integral (ac|ac) the square of a lower digit, nearly uniform on
+// [-64, 63], adds with one sign at every P: about 1365 per term, so a level sum would pass 2^24
+// (the end of exact FP32 integers) after about 12 000 terms.  Longer K is split across CTAs
+// whose exact int64 partials are added, which keeps every level sum near 2^23.
+constexpr int kExactK = 6144;
 constexpr int kFixedBase = 2 - 2 * kBeta - kFixF;  // exponent of one fixed-point unit, before row/col exponents
 constexpr size_t kDefaultBudget = 150ull << 30;
 
@@ -468,6 +474,11 @@ int run_tc(const char* name, const Ctx& c, int M, int N, int K, const Operand& A
         }
         g.epi = out.accumulate ? EPI_FP64_RMW : (intermediate ? EPI_FIXED64_RED : EPI_FIXED64);
         g.fixF = kFixF;
+        if (g.epi == EPI_FIXED64_RED && K > kExactK) {
+            // at most 64 splits: every split then still owns a non-empty K range
+            g.epi = EPI_FIXED64_ADD;
+            g.ksplit = (int)std::min<long long>(((long long)K + kExactK - 1) / kExactK, 64);
+        }
         // Final outputs with few tiles: split K so the CTAs fill whole waves (int64 adds,
         // then one conversion pass).
         if (g.epi == EPI_FIXED64) {
@@ -498,6 +509,8 @@ int run_tc(const char* name, const Ctx& c, int M, int N, int K, const Operand& A
     if (g.epi == EPI_FIXED64_ADD) {
         CC_CU(zero_out(M, N, out, st));
         CC_CU(gemm_tc(g, st));
+        // an intermediate stays int64 fixed point: its consumer applies the exponents
+        if (intermediate) return CC_OK;
         return check_cuda(fixed_to_f64(M, N, out, A.e, rowA0, B.e, rowB0, kFixedBase, st));
     }
     return check_cuda(gemm_tc(g, st));

@@ -317,3 +317,34 @@ def test_a_range_shards_assemble(dev, mode):
             # nothing outside this range's share is written
             parts += Rp
         assert rel(parts.cpu().numpy(), full.cpu().numpy()) < 1e-14
+
+
+@pytest.mark.parametrize("n", [7000, 20000])
+def test_long_cholesky_contraction(dev, oracle, n):
+    """n_chol beyond 6144: the integral builds split K across CTAs (2 and 4 splits) so that every
+    FP32 level sum stays exact.  L without decay and amplitudes diagonal in (c, d) make
+    R[i,j,a,a] = sum_c (ac|ac) t_ijcc, built only from diagonal integrals, whose lower-digit squares
+    add with one sign (without the split their level sums pass 2^24 near n = 12 000)."""
+    o, v = 2, 10
+    rng = np.random.default_rng(n)
+    L = synth.cholesky_vectors(n, v, decay=0.0, rng=rng)
+    tau = rng.standard_normal((o, o, v))
+    tau = 0.5 * (tau + tau.transpose(1, 0, 2))  # t_ijcc = t_jicc (pair symmetry)
+    t2 = np.zeros((o, o, v, v))
+    t2[:, :, np.arange(v), np.arange(v)] = tau
+    R_ref = oracle.ladder(L, t2)
+    diag = np.arange(v)
+    for mode in ("fp64", "ozaki_bf16"):
+        R = _fwd(L, t2, dev, mode=mode, symmetric=True, order="integral_first")
+        assert rel(R, R_ref) < TOL[mode], (mode, rel(R, R_ref))
+        assert rel(R[:, :, diag, diag], R_ref[:, :, diag, diag]) < TOL[mode]
+    # the Eq. 8 term's integral build and the adjoint's take the same split
+    Lov = np.ascontiguousarray(L[:, :o, :])
+    T = B.tijkl(cu(Lov, dev), cu(t2, dev), mode="ozaki_bf16").cpu().numpy()
+    assert rel(T, oracle.tijkl(Lov, t2)) < TOL["ozaki_bf16"]
+    if n == 7000:
+        W = rng.standard_normal((o, o, v, v))
+        dL_ref, dt2_ref = oracle.ladder_grad(L, t2, W)
+        dL, dt2 = B.ladder_backward(cu(L, dev), cu(t2, dev), cu(W, dev), mode="ozaki_bf16", symmetric=True)
+        assert rel(dt2.cpu().numpy(), dt2_ref) < TOL["ozaki_bf16"]
+        assert rel(dL.cpu().numpy(), dL_ref) < TOL["ozaki_bf16"]
