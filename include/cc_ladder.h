@@ -248,7 +248,10 @@ void cc_ladder_set_wait_limit_ns(unsigned long long ns);
  *   C[m*ldc + n] (= or +=) sum_k A[m*lda + k] * B[n*ldb + k]     (row-major, K-contiguous FP64)
  * in the arithmetic of `mode` (CC_FP64: DMMA; CC_OZAKI_BF16: split BF16 slices on tcgen05 with
  * FP64 recombination; CC_TF32 / CC_BF16: one rounded copy, FP32 accumulation per K-chunk).
- * accumulate != 0 adds into C.  Workspace from cc_ladder_gemm_workspace_size. */
+ * accumulate != 0 adds into C.  Workspace from cc_ladder_gemm_workspace_size.
+ * CC_OZAKI_BF16 here does not split K for exactness: where a row of A equals a row of B (the
+ * diagonal of a Gram matrix A A^T), the squares of the lower digits add with one sign and those
+ * entries lose exactness beyond K of about 12 000 (a few 1e-10 relative). */
 int cc_ladder_gemm_workspace_size(int mode, int M, int N, int K, int slices, size_t* bytes);
 int cc_ladder_gemm(int mode, int M, int N, int K, const double* A, int lda, const double* B, int ldb, double* C,
                    int ldc, int accumulate, int slices, void* workspace, size_t ws_bytes, void* stream);
