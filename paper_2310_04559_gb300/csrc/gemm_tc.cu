@@ -175,30 +175,6 @@ __device__ __forceinline__ void tma_load_3d(void* dst, const CUtensorMap* map, u
         : "memory");
 }
 
-// Multicast load: the box lands at the same shared-memory offset in every CTA of
-// `mask` and completes `bar` (same offset) in each of them.
-__device__ __forceinline__ void tma_load_3d_mc(void* dst, const CUtensorMap* map, unsigned long long* bar, int x, int y,
-                                               int z, uint16_t mask)
-{
-    asm volatile(
-        "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes.multicast::cluster"
-        " [%0], [%1, {%2, %3, %4}], [%5], %6;"
-        ::"r"(smem_u32(dst)), "l"((unsigned long long)map), "r"(x), "r"(y), "r"(z), "r"(smem_u32(bar)), "h"(mask)
-        : "memory");
-}
-
-__device__ __forceinline__ void cluster_sync()
-{
-    asm volatile("barrier.cluster.arrive.release.aligned;\nbarrier.cluster.wait.acquire.aligned;" ::: "memory");
-}
-
-__device__ __forceinline__ uint32_t cluster_rank()
-{
-    uint32_t r;
-    asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
-    return r;
-}
-
 // tcgen05 shared-memory matrix descriptor: K-major, 128-byte swizzle, 8-row
 // groups 1024 bytes apart (stride byte offset), descriptor version 1.
 __device__ __forceinline__ unsigned long long smem_desc(const void* p)
@@ -242,14 +218,6 @@ __device__ __forceinline__ void mma(uint32_t tmem_d, unsigned long long adesc, u
 __device__ __forceinline__ void mma_commit(unsigned long long* bar)
 {
     asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
-                 : "memory");
-}
-
-// Arrive on `bar` (same offset) in every CTA of `mask` once the prior MMAs complete.
-__device__ __forceinline__ void mma_commit_mc(unsigned long long* bar, uint16_t mask)
-{
-    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.multicast::cluster.b64 [%0], %1;"
-                 ::"r"(smem_u32(bar)), "h"(mask)
                  : "memory");
 }
 
@@ -319,10 +287,7 @@ struct PassIter {
     }
 };
 
-// CM: CTAs per cluster along M.  The CM CTAs of a cluster own consecutive M-tiles of
-// one N-tile; each loads 1/CM of every B slice tile and multicasts it to all of them,
-// and a B slot is refilled only after every CTA's MMAs released it.
-template <int KIND, int CM>
+template <int KIND>
 __global__ void __launch_bounds__(THREADS, 1)
 gemm_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, const Params p)
 {
@@ -335,21 +300,17 @@ gemm_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
     constexpr int KSTEP = KIND == TC_BF16 ? 64 : 32;  // K elements per 128-byte row
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
 
-    // grouped raster over clusters: consecutive clusters walk group_m cluster-rows
-    // (CM M-tiles each) before the next N-tile
-    const int rank = CM > 1 ? (int)cluster_rank() : 0;
-    const int tiles_m2 = (p.tiles_m + CM - 1) / CM;
+    // grouped raster: consecutive CTAs walk group_m M-tiles before the next N-tile
     const int per_group = p.group_m * p.tiles_n;
-    const int nclus = tiles_m2 * p.tiles_n;             // clusters per K split
-    const int split = (int)(blockIdx.x / CM) / nclus;    // this CTA's K split
-    const int t = (int)(blockIdx.x / CM) % nclus;
+    const int ntiles = p.tiles_m * p.tiles_n;            // tiles per K split
+    const int split = (int)blockIdx.x / ntiles;          // this CTA's K split
+    const int t = (int)blockIdx.x % ntiles;
     const int first_m = (t / per_group) * p.group_m;
-    const int gm = min(tiles_m2 - first_m, p.group_m);
-    const int m0 = ((first_m + (t % per_group) % gm) * CM + rank) * BM;
+    const int gm = min(p.tiles_m - first_m, p.group_m);
+    const int m0 = (first_m + (t % per_group) % gm) * BM;
     const int n0 = ((t % per_group) / gm) * BN;
-    const uint16_t cmask = (uint16_t)((1u << CM) - 1);
-    // triangular skip (the host launches CM == 1 with it): every element of the tile has
-    // b(n) < a(m), so nothing of it is needed; leave before any barrier or TMEM is touched
+    // triangular skip: every element of the tile has b(n) < a(m), so nothing of it is
+    // needed; leave before any barrier or TMEM is touched
     if (p.tri_rdiv > 0) {
         const long long nmax = min((long long)p.N - 1, (long long)n0 + BN - 1);
         if (nmax / p.tri_cdiv < (long long)m0 / p.tri_rdiv) return;
@@ -357,7 +318,7 @@ gemm_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
 
     if (threadIdx.x == 0) {
         for (int s = 0; s < NA; ++s) { mbar_init(&ctl->afull[s], 1); mbar_init(&ctl->aempty[s], ISSUERS); }
-        for (int s = 0; s < NB; ++s) { mbar_init(&ctl->bfull[s], 1); mbar_init(&ctl->bempty[s], ISSUERS * CM); }
+        for (int s = 0; s < NB; ++s) { mbar_init(&ctl->bfull[s], 1); mbar_init(&ctl->bempty[s], ISSUERS); }
         for (int b = 0; b < 2; ++b) { mbar_init(&ctl->tfull[b], 1); mbar_init(&ctl->tempty[b], EPI_WARPS); }
         for (int q = 0; q < ISSUERS; ++q) mbar_init(&ctl->drain[q], 1);
         ctl->abort = 0;
@@ -380,7 +341,6 @@ gemm_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
     }
     fence_before();
     __syncthreads();
-    if (CM > 1) cluster_sync();  // peers' barriers are initialised before any multicast reaches them
     fence_after();
     const uint32_t tmem = ctl->tmem_base;
 
@@ -425,12 +385,7 @@ gemm_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
                             break;
                         }
                         mbar_expect_tx(&ctl->bfull[bs], B_TILE);
-                        if (CM == 1) {
-                            tma_load_3d(bring + bs * B_TILE, &tmB, &ctl->bfull[bs], kb, (int)(p.rowB0 + n0), j);
-                        } else {
-                            tma_load_3d_mc(bring + bs * B_TILE + rank * (B_TILE / CM), &tmB, &ctl->bfull[bs], kb,
-                                           (int)(p.rowB0 + n0 + rank * (BN / CM)), j, cmask);
-                        }
+                        tma_load_3d(bring + bs * B_TILE, &tmB, &ctl->bfull[bs], kb, (int)(p.rowB0 + n0), j);
                         ++b_issued;
                     }
                 }
@@ -527,8 +482,7 @@ gemm_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
                                 any = true;
                             }
                         }
-                        if (CM == 1) mma_commit(&ctl->bempty[bs]);
-                        else mma_commit_mc(&ctl->bempty[bs], cmask);
+                        mma_commit(&ctl->bempty[bs]);
                         ++b_used;
                         // release the A tiles no later B of this K-step needs: i > min(hi, L2 - j - 1)
                         const int keep = j < hi ? (L2 - j - 1 < hi ? L2 - j - 1 : hi) : lo - 1;
@@ -696,7 +650,6 @@ gemm_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
 
     fence_before();
     __syncthreads();
-    if (CM > 1) cluster_sync();  // no CTA leaves while a peer may still multicast into it
     fence_after();
     if (warp == 1) {
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TMEM_COLS));
@@ -820,47 +773,22 @@ cudaError_t gemm_tc(const GemmTc& g, cudaStream_t s)
     p.wait_ns = g.wait_ns;
     p.tiles_m = (g.M + BM - 1) / BM;
     p.tiles_n = (g.N + BN - 1) / BN;
-    // CTAs per cluster along M (B multicast).  Measured on GB300 at o40/v400/n2000 the
-    // multicast costs more in coupling than it saves in L2 traffic (65.8 vs 63.6 TFLOP/s),
-    // so it is off unless CC_LADDER_TC_CLUSTER=2.
-    static const int cluster_pref = [] {
-        const char* e = getenv("CC_LADDER_TC_CLUSTER");
-        return (e && e[0] == '2') ? 2 : 1;
-    }();
-    const int CM = (p.tiles_m >= 2 && cluster_pref == 2 && p.tri_rdiv == 0) ? 2 : 1;
-    const int tiles_m2 = (p.tiles_m + CM - 1) / CM;
-    p.group_m = tiles_m2 < 8 ? tiles_m2 : 8;
+    p.group_m = p.tiles_m < 8 ? p.tiles_m : 8;
     CUtensorMap ma, mb;
     if (!make_map(&ma, g.A, g.kind, g.K, g.pitchA, g.rowsA, g.slices, BM)) return cudaErrorInvalidValue;
-    if (!make_map(&mb, g.B, g.kind, g.K, g.pitchB, g.rowsB, g.slices, BN / CM)) return cudaErrorInvalidValue;
-    const long long nctas = (long long)tiles_m2 * CM * p.tiles_n * p.ksplit;
+    if (!make_map(&mb, g.B, g.kind, g.K, g.pitchB, g.rowsB, g.slices, BN)) return cudaErrorInvalidValue;
+    const long long nctas = (long long)p.tiles_m * p.tiles_n * p.ksplit;
     if (nctas > 0x7fffffffll) return cudaErrorInvalidConfiguration;
-    cudaLaunchConfig_t cfg{};
-    cfg.gridDim = dim3((unsigned)nctas);
-    cfg.blockDim = dim3(THREADS);
-    cfg.dynamicSmemBytes = SMEM_BYTES;
-    cfg.stream = s;
-    cudaLaunchAttribute attr[1];
-    attr[0].id = cudaLaunchAttributeClusterDimension;
-    attr[0].val.clusterDim.x = CM;
-    attr[0].val.clusterDim.y = 1;
-    attr[0].val.clusterDim.z = 1;
-    cfg.attrs = attr;
-    cfg.numAttrs = CM > 1 ? 1 : 0;
     static std::once_flag once;
     std::call_once(once, [] {
-        cudaFuncSetAttribute(gemm_tc_kernel<TC_BF16, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SMEM_BYTES);
-        cudaFuncSetAttribute(gemm_tc_kernel<TC_BF16, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SMEM_BYTES);
-        cudaFuncSetAttribute(gemm_tc_kernel<TC_TF32, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SMEM_BYTES);
-        cudaFuncSetAttribute(gemm_tc_kernel<TC_TF32, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SMEM_BYTES);
+        cudaFuncSetAttribute(gemm_tc_kernel<TC_BF16>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SMEM_BYTES);
+        cudaFuncSetAttribute(gemm_tc_kernel<TC_TF32>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SMEM_BYTES);
     });
     cudaError_t err;
     if (g.kind == TC_BF16)
-        err = CM == 2 ? cudaLaunchKernelEx(&cfg, gemm_tc_kernel<TC_BF16, 2>, ma, mb, p)
-                      : cudaLaunchKernelEx(&cfg, gemm_tc_kernel<TC_BF16, 1>, ma, mb, p);
+        err = (gemm_tc_kernel<TC_BF16><<<(unsigned)nctas, THREADS, SMEM_BYTES, s>>>(ma, mb, p), cudaGetLastError());
     else
-        err = CM == 2 ? cudaLaunchKernelEx(&cfg, gemm_tc_kernel<TC_TF32, 2>, ma, mb, p)
-                      : cudaLaunchKernelEx(&cfg, gemm_tc_kernel<TC_TF32, 1>, ma, mb, p);
+        err = (gemm_tc_kernel<TC_TF32><<<(unsigned)nctas, THREADS, SMEM_BYTES, s>>>(ma, mb, p), cudaGetLastError());
     if (err != cudaSuccess) return err;
     count_launch();
     return cudaGetLastError();
