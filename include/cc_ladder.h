@@ -56,7 +56,11 @@ enum cc_status {
     CC_ERR_CUDA = -7,           /* a CUDA runtime call failed                       */
     CC_ERR_DEVICE_TIMEOUT = -8, /* a bounded device-side wait ran out; results invalid */
     CC_ERR_ARG = -9,            /* other invalid argument (unknown mode, bad a_block) */
-    CC_ERR_NOALLOC_LIMIT = -10  /* problem larger than cc_ladder_energy_noalloc's fixed scratch */
+    CC_ERR_NOALLOC_LIMIT = -10, /* problem larger than cc_ladder_energy_noalloc's fixed scratch */
+    CC_ERR_NONFINITE = -11      /* CC_OZAKI_BF16: an input (L, t2, the adjoint's dR, a GEMM operand)
+                                   holds NaN or Inf, which the integer slices cannot carry; the
+                                   outputs are invalid.  The other modes propagate NaN / Inf into
+                                   the outputs as IEEE arithmetic does and never return this. */
 };
 
 /* Arithmetic used for the two contractions (integral build and ladder GEMM). */
@@ -113,7 +117,12 @@ typedef struct cc_ladder_args {
     const double* t2;      /* device [o][o][v][v] (page-locked host memory with CC_FLAG_HOST_T2R) */
     double* R;             /* device [o][o][v][v] (host, as t2); overwritten unless
                               CC_FLAG_ACCUMULATE                                                */
-    double* energy;        /* nullable device scalar: E = sum_ijab (2 R_ijab - R_ijba) t2_ijab  */
+    double* energy;        /* nullable device scalar: E = sum_ijab (2 R_ijab - R_ijba) t2_ijab.
+                              With an a-range (a_lo, a_hi below) on the pair-symmetric
+                              integral-first path: the terms with min(a, b) in the range, whose
+                              R_ijab and R_ijba the call writes, so the energies of disjoint
+                              ranges add up to E; other paths need the complete range
+                              (CC_ERR_UNSUPPORTED otherwise).                                  */
     int mode;              /* cc_precision                                                      */
     int order;             /* cc_order                                                          */
     int a_block;           /* 0 = planner's choice; else the number of `a` values per block     */
@@ -129,8 +138,8 @@ typedef struct cc_ladder_args {
                               all i, j, a in the range and b >= a; Cholesky-first: R[i,j,a,b]
                               (i <= j) and R[j,i,b,a] (i < j) for a in the range.  Either way
                               disjoint ranges write disjoint entries, so ranges spread over
-                              devices (each R zeroed first) assemble R by a sum.  energy must
-                              be NULL unless the range is complete.                              */
+                              devices (each R zeroed first) assemble R by a sum
+                              (cc_ladder_partition balances the ranges' work).                   */
 } cc_ladder_args;
 
 /* What the planner decided for a call (for reporting and tests). */
@@ -166,6 +175,19 @@ int cc_ladder_fwd(int o, int v, int n_chol, const double* L, const double* t2, d
 
 /* Forward with every option (order, a-block, accumulate, pair symmetry, exchange, slices). */
 int cc_ladder_fwd_ex(const cc_ladder_args* args);
+
+/* Work-balanced partition of the `a` range of one problem over `parts` devices (or ranks), for
+ * running one problem on several GPUs without any exchange of data between them: part g calls
+ * cc_ladder_fwd_ex with a_lo = bounds[g], a_hi = bounds[g + 1] on its own zeroed R, the parts'
+ * R add up to the full R, and (pair-symmetric integral-first path) their energies add up to the
+ * full energy (see cc_ladder_args.energy).  The output is not part of the paper, which leaves
+ * multi-GPU execution to future work; the partition follows its for-loop over `a` (Section 3.2).
+ * Reads o, v, n_chol, mode, order and flags of `args` (pointers may be NULL).  bounds: host
+ * array of parts + 1 ints, bounds[0] = 0 < bounds[1] < ... < bounds[parts] = v.  On the packed
+ * pair-symmetric path the work of column a is proportional to v - a (it builds the integrals
+ * (a, b >= a) and their ladder columns), so the parts get equal sums of v - a; elsewhere equal
+ * counts.  CC_ERR_ARG unless 1 <= parts <= v.  Host-only: launches nothing. */
+int cc_ladder_partition(const cc_ladder_args* args, int parts, int* bounds);
 
 /* Autotuner: times both contraction orders (Section 3.2) on this shape with the caller's
  * buffers and workspace (one and two blocks of `a` per order, extrapolated to all blocks), and
@@ -273,6 +295,21 @@ typedef struct cc_ladder_profile_entry {
 void cc_ladder_profile_enable(int on);
 int cc_ladder_profile_read(cc_ladder_profile_entry* out, int max_entries);
 long long cc_ladder_launch_count(void);
+
+/* Peak-rate probes (no counterpart in the paper: measurement support, so that each precision
+ * mode's throughput can be set against the rate of the unit it runs on, measured on the same GPU).
+ * Launches one microbenchmark kernel twice (warm-up, then timed with CUDA events on `stream`,
+ * synchronised) and writes the whole GPU's rate in TFLOP/s to *tflops (host pointer).
+ *   CC_PROBE_DMMA     mma.sync.m8n8k4.f64 from registers (the FP64 mode's GEMM instruction)
+ *   CC_PROBE_DFMA     scalar FP64 fma from registers
+ *   CC_PROBE_TC_BF16  tcgen05.mma kind::f16, BF16 operands in shared memory, M=128 N=256 K=16,
+ *                     one issuing thread per SM (the emulated-FP64 and BF16 modes)
+ *   CC_PROBE_TC_TF32  tcgen05.mma kind::tf32, M=128 N=256 K=8 (the TF32 mode)
+ * iters (1 .. 2^24): loop trips per thread (tensor-core probes: groups of four MMAs).  The
+ * tensor-core probes' wait for their last MMAs is bounded (2 s, CC_ERR_DEVICE_TIMEOUT).
+ * Allocates no device memory. */
+enum cc_probe { CC_PROBE_DMMA = 1, CC_PROBE_DFMA = 2, CC_PROBE_TC_BF16 = 3, CC_PROBE_TC_TF32 = 4 };
+int cc_ladder_peak_probe(int which, int iters, void* stream, double* tflops);
 
 /* Static description of a status code. */
 const char* cc_ladder_strerror(int status);

@@ -245,6 +245,32 @@ double oracle_energy(int o, int v, const double* R, const double* t2, double* e_
 }
 
 /*
+ * The share of the pair energy that one part of an `a`-range partition owns:
+ * the terms (2 R_ijab - R_ijba) t_ijab of the sum above whose smaller virtual
+ * index min(a, b) lies in [lo, hi).  Both R_ijab and R_ijba of such a term belong
+ * to that part (the pair-symmetric path writes R[.,.,a,b] and R[.,.,b,a] for the
+ * a of its range and every b >= a), and the shares of disjoint ranges covering
+ * [0, v) add up to the full sum.  Plain loops over every (i, j, a, b), Neumaier sums.
+ */
+double oracle_energy_range(int o, int v, const double* R, const double* t2, int lo, int hi)
+{
+    const size_t vv = (size_t)v * v;
+    nsum_t tot = {0.0, 0.0};
+    for (int i = 0; i < o; ++i)
+        for (int j = 0; j < o; ++j) {
+            const size_t ij = ((size_t)i * o + j) * vv;
+            for (int a = 0; a < v; ++a)
+                for (int b = 0; b < v; ++b) {
+                    const int m = a < b ? a : b;
+                    if (m < lo || m >= hi) continue;
+                    nsum_add(&tot, (2.0 * R[ij + (size_t)a * v + b] - R[ij + (size_t)b * v + a]) *
+                                       t2[ij + (size_t)a * v + b]);
+                }
+        }
+    return nsum_get(&tot);
+}
+
+/*
  * Gradient of loss = sum_ijab W_ijab R_ijab, R from Eq. 6, with respect to
  * t2 and L, written out literally (no symmetry of L or t2 assumed):
  *

@@ -12,6 +12,7 @@ Functions (each follows the passage cited in ladder_oracle.c):
 * ``ladder_eri(L, t2)`` -- brute force through the dense integral tensor (Eq. 4/5).
 * ``ladder_entries(L, t2, idx)`` -- selected entries of Eq. 6, one by one.
 * ``energy(R, t2)`` -- E = sum (2 R_ijab - R_ijba) t_ijab.
+* ``energy_range(R, t2, lo, hi)`` -- the terms of E with min(a, b) in [lo, hi).
 * ``ladder_grad(L, t2, W)`` -- dt2, dL of loss = <W, R>.
 * ``ladder_grad_entries(...)`` -- selected gradient entries.
 * ``exchange(L, t2, a_list=None)`` -- Eq. 7.
@@ -57,6 +58,8 @@ def _load():
                                                                    ctypes.c_int, _dp, ctypes.c_int]
         lib.oracle_energy.argtypes = [ctypes.c_int, ctypes.c_int, _dp, _dp, _dp]
         lib.oracle_energy.restype = ctypes.c_double
+        lib.oracle_energy_range.argtypes = [ctypes.c_int, ctypes.c_int, _dp, _dp, ctypes.c_int, ctypes.c_int]
+        lib.oracle_energy_range.restype = ctypes.c_double
         lib.oracle_ladder_grad.argtypes = [ctypes.c_int] * 3 + [_dp, _dp, _dp, _dp, _dp, ctypes.c_int]
         _llp = ctypes.POINTER(ctypes.c_longlong)
         lib.oracle_ladder_grad_entries.argtypes = ([ctypes.c_int] * 3 + [_dp, _dp, _dp, _llp, ctypes.c_int, _dp,
@@ -136,6 +139,16 @@ def energy(R, t2, pair=False):
     ep = np.empty((o, o)) if pair else None
     e = lib.oracle_energy(o, v, _p(R), _p(t2), _p(ep))
     return (e, ep) if pair else e
+
+
+def energy_range(R, t2, lo, hi):
+    """Terms of the pair energy with min(a, b) in [lo, hi): one part's share under an
+    `a`-range partition of the pair-symmetric path."""
+    lib = _load()
+    R, t2 = _f64(R), _f64(t2)
+    o, v = t2.shape[0], t2.shape[2]
+    assert R.shape == t2.shape
+    return lib.oracle_energy_range(o, v, _p(R), _p(t2), int(lo), int(hi))
 
 
 def ladder_grad(L, t2, W, want_dL=True, want_dt2=True, threads=0):

@@ -15,7 +15,7 @@ CC_OK = 0
 STATUS = {
     0: "CC_OK", -1: "CC_ERR_SHAPE", -2: "CC_ERR_NULL", -3: "CC_ERR_ALIGN", -4: "CC_ERR_WORKSPACE",
     -5: "CC_ERR_BUDGET", -6: "CC_ERR_UNSUPPORTED", -7: "CC_ERR_CUDA", -8: "CC_ERR_DEVICE_TIMEOUT", -9: "CC_ERR_ARG",
-    -10: "CC_ERR_NOALLOC_LIMIT",
+    -10: "CC_ERR_NOALLOC_LIMIT", -11: "CC_ERR_NONFINITE",
 }
 MODES = {"fp64": 0, "ozaki_bf16": 1, "ozaki_int8": 2, "tf32": 3, "bf16": 4}
 ORDERS = {"auto": 0, "integral_first": 1, "cholesky_first": 2}
@@ -65,9 +65,10 @@ SYMBOLS = [
     "cc_ladder_energy_workspace_size", "cc_ladder_device_status", "cc_ladder_set_wait_limit_ns",
     "cc_ladder_strerror", "cc_ladder_version", "cc_ladder_gemm_workspace_size", "cc_ladder_gemm",
     "cc_ladder_profile_enable", "cc_ladder_profile_read", "cc_ladder_launch_count", "cc_ladder_energy_noalloc",
-    "cc_ladder_autotune", "cc_ladder_term_workspace_size", "cc_ladder_term", "cc_ladder_tijkl", "cc_ladder_tijbk",
+    "cc_ladder_autotune", "cc_ladder_partition", "cc_ladder_peak_probe", "cc_ladder_term_workspace_size", "cc_ladder_term", "cc_ladder_tijkl", "cc_ladder_tijbk",
 ]
 TERMS = {"ijkl": 1, "ijbk": 2}
+PROBES = {"dmma": 1, "dfma": 2, "tc_bf16": 3, "tc_tf32": 4}
 
 
 def lib_path() -> str:
@@ -108,6 +109,8 @@ def load(build_if_missing: bool = True):
     L.cc_ladder_energy_noalloc.argtypes = [_i, _i, _vp, _vp, _vp, _vp, _vp]
     L.cc_ladder_autotune.argtypes = [ctypes.POINTER(Args), ctypes.POINTER(Plan), ctypes.POINTER(ctypes.c_double),
                                       ctypes.POINTER(ctypes.c_double)]
+    L.cc_ladder_peak_probe.argtypes = [_i, _i, _vp, ctypes.POINTER(ctypes.c_double)]
+    L.cc_ladder_partition.argtypes = [ctypes.POINTER(Args), _i, ctypes.POINTER(_i)]
     L.cc_ladder_term_workspace_size.argtypes = [_i, _i, _i, _i, _i, _i, _sz, ctypes.POINTER(_sz)]
     L.cc_ladder_term.argtypes = [_i, _i, _i, _i, _vp, _vp, _vp, _vp, _i, _i, _i, _vp, _sz, _vp]
     L.cc_ladder_tijkl.argtypes = [_i, _i, _i, _vp, _vp, _vp, _i, _vp, _sz, _vp]

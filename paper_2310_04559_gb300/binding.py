@@ -107,6 +107,17 @@ def plan(o, v, n, ws_bytes=0, **kw) -> dict:
             "flops_algorithmic": p.flops_algorithmic, "flops_issued": p.flops_issued, "pair_blocks": p.pair_blocks}
 
 
+def partition(o, v, n, parts, **kw) -> list:
+    """Work-balanced bounds [0 = b_0 < b_1 < ... < b_parts = v] of the `a` range of one problem
+    over `parts` devices (keywords as in make_args): part g computes a_range=(b_g, b_g+1).
+    Host-only; no device is touched."""
+    lib = _lib.load()
+    a = make_args(o, v, n, **kw)
+    out = (ctypes.c_int * (parts + 1))()
+    _lib.check(lib.cc_ladder_partition(ctypes.byref(a), int(parts), out), "cc_ladder_partition")
+    return list(out)
+
+
 def autotune(L, t2, R=None, mode="ozaki_bf16", symmetric=False, exchange=False, slices=0, budget=0,
              workspace=None) -> dict:
     """Time both contraction orders on this shape and record the faster one for
@@ -272,6 +283,17 @@ def gemm(A, B, mode="ozaki_bf16", C=None, accumulate=False, slices=0):
     _lib.check(lib.cc_ladder_gemm(_mode(mode), M, N, K, _ptr(A), K, _ptr(B), K, _ptr(C), N, int(accumulate),
                                   int(slices), _ptr(w), w.numel(), _stream(A.device)), "cc_ladder_gemm")
     return C
+
+
+def peak_probe(which, iters=0, device=None) -> float:
+    """Measured peak rate (TFLOP/s of the whole GPU) of one arithmetic unit: "dmma", "dfma",
+    "tc_bf16" or "tc_tf32" (see cc_ladder_peak_probe)."""
+    lib = _lib.load()
+    default_iters = {"dmma": 4096, "dfma": 16384, "tc_bf16": 20000, "tc_tf32": 10000}
+    out = ctypes.c_double()
+    _lib.check(lib.cc_ladder_peak_probe(_lib.PROBES[which], int(iters or default_iters[which]), _stream(device),
+                                        ctypes.byref(out)), "cc_ladder_peak_probe")
+    return out.value
 
 
 def profile_enable(on=True):

@@ -86,6 +86,7 @@ struct Ctx {
     long long Kp, Km; // packed path: v(v+1)/2 and v(v-1)/2
     bool host;        // t2 and R are page-locked host memory, read and written over the host link
     long long PB;     // packed path: pairs (i <= j) per pair block (o(o+1)/2 unless host)
+    int* status = nullptr;  // device status word of the call (the splits flag non-finite inputs there)
 };
 
 // Blocks of `a` values [a0, a0 + Ab) covering [alo, ahi).  Unpacked paths: Ab = P
@@ -382,6 +383,14 @@ int run_f64(const char* name, const GemmF64& g, cudaStream_t st, double elems = 
     } while (0)
 #define CC_CU(x) CC_TRY(check_cuda(x))
 
+// cc_status of a device status word: an expired wait first, then non-finite input.
+int status_of(int h)
+{
+    if (h & (kStatusWaitExpired | kStatusDrainExpired)) return CC_ERR_DEVICE_TIMEOUT;
+    if (h & kStatusNonfinite) return CC_ERR_NONFINITE;
+    return CC_OK;
+}
+
 int finish(void* ws_status, int flags, cudaStream_t s)
 {
     CC_CU(cudaGetLastError());
@@ -389,7 +398,7 @@ int finish(void* ws_status, int flags, cudaStream_t s)
     CC_CU(cudaStreamSynchronize(s));
     int h = 0;
     CC_CU(cudaMemcpy(&h, ws_status, sizeof(int), cudaMemcpyDeviceToHost));
-    return h ? CC_ERR_DEVICE_TIMEOUT : CC_OK;
+    return status_of(h);
 }
 
 // ---------------------------------------------------- tensor-core operand prep
@@ -404,7 +413,7 @@ int prep_rows(const Ctx& c, const RowSrc& src, Operand& op, cudaStream_t st)
     op.pitch = pitch_for(src.K, esz_of(c.mode));
     if (c.mode == CC_TF32) return check_cuda(convert_rows_tf32(src, (float*)op.D, op.pitch, st));
     const int s = c.mode == CC_OZAKI_BF16 ? c.s : 0;
-    return check_cuda(split_rows_bf16(src, s, kBeta, op.D, op.pitch, op.e, st));
+    return check_cuda(split_rows_bf16(src, s, kBeta, op.D, op.pitch, op.e, c.status, st));
 }
 
 // Split of an intermediate left as int64 fixed point by run_tc(..., intermediate=true).
@@ -424,7 +433,7 @@ int prep_cols(const Ctx& c, const ColSrc& src, Operand& op, unsigned long long* 
     op.pitch = pitch_for(src.K, esz_of(c.mode));
     if (c.mode == CC_TF32) return check_cuda(convert_cols_tf32(src, (float*)op.D, op.pitch, st));
     const int s = c.mode == CC_OZAKI_BF16 ? c.s : 0;
-    return check_cuda(split_cols_bf16(src, s, kBeta, op.D, op.pitch, op.e, colmax, st));
+    return check_cuda(split_cols_bf16(src, s, kBeta, op.D, op.pitch, op.e, colmax, c.status, st));
 }
 
 double tc_products(const Ctx& c) { return c.mode == CC_OZAKI_BF16 ? c.s * (c.s + 1) / 2.0 : 1.0; }
@@ -563,10 +572,10 @@ int fwd_packed(const Ctx& c, const cc_ladder_args* a, const double* Lsrc, const 
         const long long s0 = strict_before(q0), s1 = strict_before(q1);
         Tp.rows = q1 - q0;
         Tm.rows = s1 - s0;
-        CC_CU(pm_split_f64(t2, pairtab + q0, 1, q1 - q0, c.v, +1, 1.0, kind, c.s, kBeta, Tp.D, Tp.pitch, Tp.e, st));
+        CC_CU(pm_split_f64(t2, pairtab + q0, 1, q1 - q0, c.v, +1, 1.0, kind, c.s, kBeta, Tp.D, Tp.pitch, Tp.e, c.status, st));
         if (minus && s1 > s0)
             CC_CU(pm_split_f64(t2, pairtab_m + s0, 1, s1 - s0, c.v, -1, 1.0, kind, c.s, kBeta, Tm.D, Tm.pitch, Tm.e,
-                               st));
+                               c.status, st));
         return CC_OK;
     };
     if (pblocks.size() == 1) CC_TRY(split_t(0, c.pp));
@@ -601,9 +610,9 @@ int fwd_packed(const Ctx& c, const cc_ladder_args* a, const double* Lsrc, const 
                               Lw.e, split_map(Nb, 0, v, (long long)a0 * v), kFixedBase};
                 CC_CU(pm_split_fixed(fs, c.s, kBeta, Vp.D, Vp.pitch, Vp.e, minus ? Vm.D : nullptr, Vm.pitch, Vm.e, st));
             } else {
-                CC_CU(pm_split_f64(V, rtab, vv, nr, c.v, +1, 0.5, kind, c.s, kBeta, Vp.D, Vp.pitch, Vp.e, st));
+                CC_CU(pm_split_f64(V, rtab, vv, nr, c.v, +1, 0.5, kind, c.s, kBeta, Vp.D, Vp.pitch, Vp.e, nullptr, st));
                 if (minus)
-                    CC_CU(pm_split_f64(V, rtab, vv, nr, c.v, -1, 0.5, kind, c.s, kBeta, Vm.D, Vm.pitch, Vm.e, st));
+                    CC_CU(pm_split_f64(V, rtab, vv, nr, c.v, -1, 0.5, kind, c.s, kBeta, Vm.D, Vm.pitch, Vm.e, nullptr, st));
             }
         }
         OutDesc op{Rpc, plain_map(nr), plain_map(1), 0};
@@ -672,8 +681,11 @@ int fwd_impl(const cc_ladder_args* a, const double* Lsrc_override = nullptr)
     cudaStream_t st = (cudaStream_t)a->stream;
     const long long o = c.o, v = c.v, n = c.n, vv = v * v;
     int* status = at<int>(ws, Lo.status);
+    c.status = status;
     const int alo = a->a_hi ? a->a_lo : 0, ahi = a->a_hi ? a->a_hi : c.v;
-    if (a->energy && (alo != 0 || ahi != c.v)) return CC_ERR_UNSUPPORTED;
+    // an a-range's share of the energy is defined where the range owns both R_ijab and R_ijba of
+    // its terms: the packed path (entries with min(a, b) in the range)
+    if (a->energy && (alo != 0 || ahi != c.v) && !c.packed) return CC_ERR_UNSUPPORTED;
     CC_CU(cudaMemsetAsync(status, 0, 256, st));
 
     const double* t2 = a->t2;
@@ -685,8 +697,9 @@ int fwd_impl(const cc_ladder_args* a, const double* Lsrc_override = nullptr)
         CC_TRY(fwd_packed(c, a, Lsrc, t2, Pblk, Lo, ws, status, st, alo, ahi));
         if (a->energy) {
             ProfScope ps("energy", st);
-            CC_CU(energy_pairs(c.o, c.v, a->R, a->t2, at<double>(ws, Lo.epart), at<double>(ws, Lo.epair), st));
-            CC_CU(energy_total(c.o * c.o, at<double>(ws, Lo.epair), a->energy, st));
+            CC_CU(energy_pairs(c.o, c.v, a->R, a->t2, at<double>(ws, Lo.epart), at<double>(ws, Lo.epair), st, alo,
+                               ahi));
+            CC_CU(energy_total((long long)c.o * c.o, at<double>(ws, Lo.epair), a->energy, st));
         }
         return finish(status, c.flags, st);
     }
@@ -811,7 +824,7 @@ int fwd_impl(const cc_ladder_args* a, const double* Lsrc_override = nullptr)
     if (a->energy) {
         ProfScope ps("energy", st);
         CC_CU(energy_pairs(c.o, c.v, a->R, a->t2, at<double>(ws, Lo.epart), at<double>(ws, Lo.epair), st));
-        CC_CU(energy_total(c.o * c.o, at<double>(ws, Lo.epair), a->energy, st));
+        CC_CU(energy_total((long long)c.o * c.o, at<double>(ws, Lo.epair), a->energy, st));
     }
     return finish(status, c.flags, st);
 }
@@ -901,7 +914,7 @@ int term_impl(int which, int o, int v, int n, const double* Lov, const double* L
     if (!A || !Bm || !t2 || !T || !ws) return CC_ERR_NULL;
     if (!aligned(A, 16) || !aligned(Bm, 16) || !aligned(t2, 16) || !aligned(T, 16) || !aligned(ws, 256))
         return CC_ERR_ALIGN;
-    const Ctx& c = tc.c;
+    Ctx c = tc.c;
     if (is_tc(c.mode) && !tc_gemm_available()) return CC_ERR_UNSUPPORTED;
     size_t need = 0;
     const long long Pb = pick_term_block(tc, ws_bytes, &need);
@@ -910,6 +923,7 @@ int term_impl(int which, int o, int v, int n, const double* Lov, const double* L
     cudaStream_t st = (cudaStream_t)stream;
     const long long v_ = v, vv = v_ * v, np_ = tc.np_, nq = tc.nq;
     int* status = at<int>(ws, Lo.status);
+    c.status = status;
     CC_CU(cudaMemsetAsync(status, 0, 256, st));
     double* V = at<double>(ws, Lo.V);
     Operand Aw{}, Bw{}, tw{}, Vw{};
@@ -1058,11 +1072,12 @@ int bwd_impl(int o, int v, int n, const double* L, const double* t2, const doubl
         return CC_ERR_ALIGN;
     CC_TRY(bwd_plan(o, v, n, mode, flags, slices, ws_bytes, false, &bp));
     if (is_tc(mode) && !tc_gemm_available()) return CC_ERR_UNSUPPORTED;
-    const Ctx& c = bp.c;
+    Ctx c = bp.c;
     const BwdLayout& Lo = bp.L;
     cudaStream_t st = (cudaStream_t)stream;
     const long long vv = (long long)v * v, P = (long long)o * o;
     int* status = at<int>(ws, Lo.status);
+    c.status = status;
     CC_CU(cudaMemsetAsync(status, 0, 256, st));
     const bool sym = (flags & CC_FLAG_SYMMETRIC_T) != 0;
 
@@ -1154,7 +1169,7 @@ int bwd_impl(int o, int v, int n, const double* L, const double* t2, const doubl
     CC_CU(cudaStreamSynchronize(st));
     int h[2] = {0, 0};
     CC_CU(cudaMemcpy(h, status, sizeof(h), cudaMemcpyDeviceToHost));
-    return (h[0] | h[1]) ? CC_ERR_DEVICE_TIMEOUT : CC_OK;
+    return status_of(h[0] | h[1]);
 }
 
 }  // namespace
@@ -1176,6 +1191,7 @@ const char* cc_ladder_strerror(int status)
     case CC_ERR_DEVICE_TIMEOUT: return "a bounded device-side wait expired; results are invalid";
     case CC_ERR_ARG: return "invalid argument";
     case CC_ERR_NOALLOC_LIMIT: return "problem exceeds the fixed scratch of cc_ladder_energy_noalloc";
+    case CC_ERR_NONFINITE: return "an input holds NaN or Inf (emulated FP64 mode); results are invalid";
     default: return "unknown status";
     }
 }
@@ -1243,6 +1259,35 @@ int cc_ladder_plan_query(const cc_ladder_args* args, cc_ladder_plan* plan)
 }
 
 int cc_ladder_fwd_ex(const cc_ladder_args* args) { return fwd_impl(args); }
+
+int cc_ladder_partition(const cc_ladder_args* args, int parts, int* bounds)
+{
+    if (!bounds) return CC_ERR_NULL;
+    Ctx c;
+    CC_TRY(make_ctx(args, &c));
+    if (parts < 1 || parts > c.v) return CC_ERR_ARG;
+    // Work of the `a` values below a: on the packed path a column a builds the integrals (a, b >= a)
+    // and the ladder columns of the same pairs, so its work is proportional to v - a; on the other
+    // paths every `a` costs the same.
+    const double v = c.v;
+    auto W = [&](int a) { return c.packed ? (double)a * v - (double)a * (a - 1) / 2.0 : (double)a; };
+    const double total = W(c.v);
+    bounds[0] = 0;
+    for (int g = 1; g < parts; ++g) {
+        const double target = total * g / parts;
+        // candidates keep every part non-empty: bounds[g-1] < a <= v - (parts - g)
+        int lo = bounds[g - 1] + 1, hi = c.v - (parts - g);
+        while (lo < hi) {  // smallest a in [lo, hi] with W(a) >= target
+            const int mid = (lo + hi) / 2;
+            if (W(mid) >= target) hi = mid; else lo = mid + 1;
+        }
+        int a = lo;
+        if (a - 1 > bounds[g - 1] && std::fabs(W(a - 1) - target) < std::fabs(W(a) - target)) --a;
+        bounds[g] = a;
+    }
+    bounds[parts] = c.v;
+    return CC_OK;
+}
 
 int cc_ladder_autotune(const cc_ladder_args* args, cc_ladder_plan* plan, double* ms_if, double* ms_cf)
 {
@@ -1338,7 +1383,7 @@ int cc_ladder_bwd(int o, int v, int n_chol, const double* L, const double* t2, c
 int cc_ladder_energy_workspace_size(int o, int v, size_t* bytes)
 {
     if (!bytes) return CC_ERR_NULL;
-    if (o < 1 || v < 1) return CC_ERR_SHAPE;
+    if (o < 1 || v < 1 || o > 46340 || v > 46340) return CC_ERR_SHAPE;
     *bytes = al256(8 * (size_t)energy_scratch_doubles(o, v)) + al256(8 * (size_t)o * o);
     return CC_OK;
 }
@@ -1346,7 +1391,7 @@ int cc_ladder_energy_workspace_size(int o, int v, size_t* bytes)
 int cc_ladder_energy(int o, int v, const double* R, const double* t2, double* energy, double* e_pair, void* workspace,
                      size_t ws_bytes, void* stream)
 {
-    if (o < 1 || v < 1) return CC_ERR_SHAPE;
+    if (o < 1 || v < 1 || o > 46340 || v > 46340) return CC_ERR_SHAPE;
     if (!R || !t2 || !energy || !workspace) return CC_ERR_NULL;
     if (!aligned(R, 16) || !aligned(t2, 16) || !aligned(workspace, 256) || !aligned(energy, 8)) return CC_ERR_ALIGN;
     size_t need = 0;
@@ -1356,7 +1401,7 @@ int cc_ladder_energy(int o, int v, const double* R, const double* t2, double* en
     double* part = (double*)workspace;
     double* ep = e_pair ? e_pair : (double*)((char*)workspace + al256(8 * (size_t)energy_scratch_doubles(o, v)));
     CC_CU(energy_pairs(o, v, R, t2, part, ep, st));
-    CC_CU(energy_total(o * o, ep, energy, st));
+    CC_CU(energy_total((long long)o * o, ep, energy, st));
     CC_CU(cudaGetLastError());
     return CC_OK;
 }
@@ -1411,6 +1456,7 @@ int cc_ladder_gemm(int mode, int M, int N, int K, const double* A, int lda, cons
         Ctx c{};
         c.mode = mode;
         c.s = slices_of(mode, slices);
+        c.status = status;
         const int es = esz_of(mode);
         Carve cv;
         cv.take(256);
@@ -1465,7 +1511,7 @@ int cc_ladder_device_status(void* workspace, void* stream)
     int h[2] = {0, 0};
     CC_CU(cudaMemcpy(h, workspace, sizeof(h), cudaMemcpyDeviceToHost));
     CC_CU(cudaMemset(workspace, 0, sizeof(h)));
-    return (h[0] | h[1]) ? CC_ERR_DEVICE_TIMEOUT : CC_OK;
+    return status_of(h[0] | h[1]);
 }
 
 }  // extern "C"

@@ -9,6 +9,11 @@
 
 namespace cc {
 
+// Bits of the device status word at the start of every workspace.
+constexpr int kStatusWaitExpired = 1;   // a bounded device-side wait ran out
+constexpr int kStatusDrainExpired = 2;  // the abort path's drain ran out as well
+constexpr int kStatusNonfinite = 16;    // an Ozaki split met NaN or Inf in its FP64 input
+
 // Two-level index map: off(i) = (i / div) * s0 + (i % div) * s1 + base, where the
 // outer term is tab[i / div] instead when a device table is given.  div == 0 means
 // a plain stride: off(i) = i * s1 + base (or tab[i] + base).
@@ -107,7 +112,9 @@ struct RowSrc {
 // Ozaki split of each row into `s` balanced base-2^beta digits stored as bf16 in
 // D[s][rows][pitch] with exponent e[r] (max |row| < 2^e).  s == 0: plain bf16 copy
 // (e = 0).  D must hold s*rows*pitch bf16.
-cudaError_t split_rows_bf16(const RowSrc& src, int s, int beta, void* D, long long pitch, int* e, cudaStream_t st);
+// status (nullable): kStatusNonfinite is or-ed in when a split row holds NaN or Inf (s > 0).
+cudaError_t split_rows_bf16(const RowSrc& src, int s, int beta, void* D, long long pitch, int* e, int* status,
+                            cudaStream_t st);
 // Column source, rows contiguous: X(r, k) = X[bmap(r / brows) + r % brows + k * ldk]
 // for r in [0, rows); brows == 0 means one batch (X[r + k * ldk]).
 struct ColSrc {
@@ -115,7 +122,7 @@ struct ColSrc {
     long long brows; Map2 bmap;
 };
 cudaError_t split_cols_bf16(const ColSrc& src, int s, int beta, void* D, long long pitch, int* e,
-                            unsigned long long* scratch_max, cudaStream_t st);
+                            unsigned long long* scratch_max, int* status, cudaStream_t st);
 // Ozaki split of an int64 fixed-point intermediate (a slice-GEMM output kept as
 // EPI_FIXED64_RED).  Row r, element k = o*inner + i is X[r*ldx + k] * 2^e with
 // e = eA[amap(r) + o] + eB[bmap(r) + i] + base.  Integer arithmetic only.
@@ -133,8 +140,10 @@ cudaError_t split_fixed_rows_bf16(const FixedSrc& src, int s, int beta, void* D,
 // sign > 0 writes the c <= d part (X[c][d] + X[d][c]) * h (diagonal X[c][c]) at c*v - c(c-1)/2 + d - c,
 // sign < 0 the c < d part (X[c][d] - X[d][c]) * h at c*(v-1) - c(c-1)/2 + d - c - 1.  kind 0: Ozaki
 // digits with a row exponent, 1: bf16 copy (e = 0), 2: tf32 copy (e may be NULL), 3: FP64 copy.
+// status (nullable, kind 0): kStatusNonfinite is or-ed in when a packed row holds NaN or Inf.
 cudaError_t pm_split_f64(const double* X, const long long* rowtab, long long rowmul, long long rows, int v, int sign,
-                         double h, int kind, int s, int beta, void* D, long long pitch, int* e, cudaStream_t st);
+                         double h, int kind, int s, int beta, void* D, long long pitch, int* e, int* status,
+                         cudaStream_t st);
 // Int64 fixed-point integral block: packed row r is unpacked row ru = rtab[r] of X (ldx per row),
 // X[c][d] * 2^(eA[amap(ru) + c] + eB[bmap(ru) + d] + base).  Writes V+ (h = 1/2) and, if Dm is not
 // NULL, V- digits, both with the row exponent of max |V|.
@@ -175,9 +184,11 @@ cudaError_t fill_pair_table(int o, int v, long long* tab, cudaStream_t s);
 cudaError_t transpose_last2(long long batch, int v, const double* X, double* Y, cudaStream_t s);
 // energy
 // part: o*o*ceil(v/32)^2 doubles of scratch; e_pair: o*o results
-cudaError_t energy_pairs(int o, int v, const double* R, const double* t2, double* part, double* e_pair, cudaStream_t s);
+// Terms with lo <= min(a, b) < hi only (hi < 0: all of them).
+cudaError_t energy_pairs(int o, int v, const double* R, const double* t2, double* part, double* e_pair, cudaStream_t s,
+                         int lo = 0, int hi = -1);
 inline long long energy_scratch_doubles(int o, int v) { const long long t = (v + 31) / 32; return (long long)o * o * t * t; }
-cudaError_t energy_total(int npairs, const double* e_pair, double* E, cudaStream_t s);
+cudaError_t energy_total(long long npairs, const double* e_pair, double* E, cudaStream_t s);
 
 // ------------------------------------------------------------------- tracing
 void count_launch(int n = 1);

@@ -58,7 +58,9 @@ __global__ void __launch_bounds__(THREADS) gemm_f64_kernel(const GemmF64 g)
     __shared__ double As[2][BKT][BM + 1];
     __shared__ double Bs[2][BKT][BN + 1];
 
-    const int m0 = blockIdx.y * BM, n0 = blockIdx.x * BN;
+    // one-dimensional grid over the tiles (no gridDim.y limit on M)
+    const int tiles_n = (g.N + BN - 1) / BN;
+    const int m0 = (int)(blockIdx.x / tiles_n) * BM, n0 = (int)(blockIdx.x % tiles_n) * BN;
     if (g.tri > 0 && (long long)min(g.N - 1, n0 + BN - 1) / g.tri < (long long)m0 / g.tri) return;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int wm = (warp >> 1) * 32, wn = (warp & 1) * 32;
@@ -133,8 +135,9 @@ cudaError_t gemm_f64(const GemmF64& g, cudaStream_t s)
     if (g.M <= 0 || g.N <= 0) return cudaSuccess;
     const bool ak = (g.ak.div == 0 && !g.ak.tab && g.ak.s1 == 1);
     const bool bk = (g.bk.div == 0 && !g.bk.tab && g.bk.s1 == 1);
-    dim3 grid((g.N + BN - 1) / BN, (g.M + BM - 1) / BM);
-    if (grid.y > 65535) return cudaErrorInvalidConfiguration;
+    const long long tiles = (long long)((g.N + BN - 1) / BN) * ((g.M + BM - 1) / BM);
+    if (tiles > 0x7fffffffll) return cudaErrorInvalidConfiguration;
+    const dim3 grid((unsigned)tiles);
     if (ak && bk) gemm_f64_kernel<true, true><<<grid, THREADS, 0, s>>>(g);
     else if (ak && !bk) gemm_f64_kernel<true, false><<<grid, THREADS, 0, s>>>(g);
     else if (!ak && bk) gemm_f64_kernel<false, true><<<grid, THREADS, 0, s>>>(g);

@@ -19,16 +19,21 @@ __device__ __forceinline__ void pair_of(int o, int p, int& i, int& j)
     j = ii + rem;
 }
 
-// E_ij = sum_ab (2 R_ijab - R_ijba) t_ijab for one (i,j) per blockIdx.y, partial
-// per 32x32 (a,b) tile row written to part[ij][tile]; a second kernel sums them.
-__global__ void energy_tiles_kernel(int v, const double* __restrict__ R, const double* __restrict__ t2,
-                                    double* __restrict__ part)
+// Index of this block in a batch spread over gridDim.y x gridDim.z (see batch_grid).
+__device__ __forceinline__ long long batch_index() { return (long long)blockIdx.y + (long long)blockIdx.z * gridDim.y; }
+
+// E_ij = sum_ab (2 R_ijab - R_ijba) t_ijab for one (i,j) per batch index, over the terms
+// with lo <= min(a, b) < hi (all of them for lo = 0, hi = v); partial per 32x32 (a,b) tile
+// written to part[ij][tile]; a second kernel sums them.
+__global__ void energy_tiles_kernel(long long npairs, int v, int lo, int hi, const double* __restrict__ R,
+                                    const double* __restrict__ t2, double* __restrict__ part)
 {
     __shared__ double Rt[T][T + 1];
     __shared__ double red[T * TR];
+    const long long ij = batch_index();
+    if (ij >= npairs) return;
     const int ntile = (v + T - 1) / T;
     const int ta = blockIdx.x / ntile, tb = blockIdx.x % ntile;
-    const long long ij = blockIdx.y;
     const double* Rij = R + ij * (long long)v * v;
     const double* tij = t2 + ij * (long long)v * v;
     const int a0 = ta * T, b0 = tb * T;
@@ -41,7 +46,8 @@ __global__ void energy_tiles_kernel(int v, const double* __restrict__ R, const d
     double s = 0.0;
     for (int y = threadIdx.y; y < T; y += TR) {
         const int a = a0 + y, b = b0 + threadIdx.x;
-        if (a < v && b < v) {
+        const int m = a < b ? a : b;  // terms owned by the range [lo, hi): min(a, b) inside it
+        if (a < v && b < v && m >= lo && m < hi) {
             const long long q = (long long)a * v + b;
             s += (2.0 * Rij[q] - Rt[threadIdx.x][y]) * tij[q];
         }
@@ -53,7 +59,7 @@ __global__ void energy_tiles_kernel(int v, const double* __restrict__ R, const d
         if (tid < w) red[tid] += red[tid + w];
         __syncthreads();
     }
-    if (tid == 0) part[ij * gridDim.x + blockIdx.x] = red[0];
+    if (tid == 0) part[ij * (long long)gridDim.x + blockIdx.x] = red[0];
 }
 
 // Deterministic sum of `len` values per row of `x` (rows = gridDim.x) into y.
@@ -78,7 +84,7 @@ __global__ void transpose_kernel(long long batch, int v, const double* __restric
     __shared__ double S[T][T + 1];
     const int ntile = (v + T - 1) / T;
     const int tr = blockIdx.x / ntile, tc = blockIdx.x % ntile;
-    const long long b = (long long)blockIdx.y + (long long)blockIdx.z * gridDim.y;
+    const long long b = batch_index();
     if (b >= batch) return;
     const double* Xb = X + b * (long long)v * v;
     double* Yb = Y + b * (long long)v * v;
@@ -99,10 +105,12 @@ __global__ void scatter_pairs_kernel(int o, int v, int a_lo, int a_hi, const dou
                                      double* __restrict__ R, int accumulate)
 {
     __shared__ double S[T][T + 1];
+    const long long pb = batch_index();
+    if (pb >= (long long)o * (o + 1) / 2) return;  // uniform over the block
     const int ntile = (v + T - 1) / T;
     const int ta = blockIdx.x / ntile, tb = blockIdx.x % ntile;
     const int a0 = a_lo + ta * T;
-    const int p = blockIdx.y;
+    const int p = (int)pb;
     int i, j;
     pair_of(o, p, i, j);
     const long long vv = (long long)v * v;
@@ -134,10 +142,11 @@ __global__ void scatter_pairs_kernel(int o, int v, int a_lo, int a_hi, const dou
 __global__ void add_pair_swap_kernel(int o, int v, const double* __restrict__ X, double* __restrict__ Y, int alpha)
 {
     __shared__ double S[T][T + 1];
+    const long long ij = batch_index();
+    if (ij >= (long long)o * o) return;
     const int ntile = (v + T - 1) / T;
     const int ta = blockIdx.x / ntile, tb = blockIdx.x % ntile;
-    const int ij = blockIdx.y;
-    const int i = ij / o, j = ij % o;
+    const int i = (int)(ij / o), j = (int)(ij % o);
     const long long vv = (long long)v * v;
     const double* Xji = X + ((long long)j * o + i) * vv;
     const double* Xij = X + (long long)ij * vv;
@@ -166,26 +175,31 @@ __global__ void fill_pair_table_kernel(int o, long long vv, long long* tab)
     tab[p] = ((long long)i * o + j) * vv;
 }
 
+// Grid for `batch` independent blocks of ntile2 tiles: batch index = y + z * gridDim.y, with
+// gridDim.y and gridDim.z within the 65535 limit for any batch up to 65535^2 (blocks with an
+// index beyond the batch return at once).
 dim3 batch_grid(int ntile2, long long batch)
 {
-    long long gy = batch, gz = 1;
-    while (gy > 65535) { gz *= 2; gy = (batch + gz - 1) / gz; }
-    return dim3(ntile2, (unsigned)gy, (unsigned)gz);
+    const long long gz = (batch + 65534) / 65535;
+    const long long gy = (batch + gz - 1) / gz;
+    return dim3(ntile2, (unsigned)(gy > 0 ? gy : 1), (unsigned)(gz > 0 ? gz : 1));
 }
 
 }  // namespace
 
 cudaError_t energy_pairs(int o, int v, const double* R, const double* t2, double* part, double* e_pair,
-                         cudaStream_t s)
+                         cudaStream_t s, int lo, int hi)
 {
+    if (hi < 0) hi = v;
     const int ntile = (v + T - 1) / T;
-    energy_tiles_kernel<<<dim3(ntile * ntile, o * o), dim3(T, TR), 0, s>>>(v, R, t2, part);
-    row_sum_kernel<<<o * o, 256, 0, s>>>((long long)ntile * ntile, part, e_pair);
+    const long long np = (long long)o * o;
+    energy_tiles_kernel<<<batch_grid(ntile * ntile, np), dim3(T, TR), 0, s>>>(np, v, lo, hi, R, t2, part);
+    row_sum_kernel<<<(unsigned)np, 256, 0, s>>>((long long)ntile * ntile, part, e_pair);
     count_launch(2);
     return cudaGetLastError();
 }
 
-cudaError_t energy_total(int npairs, const double* e_pair, double* E, cudaStream_t s)
+cudaError_t energy_total(long long npairs, const double* e_pair, double* E, cudaStream_t s)
 {
     row_sum_kernel<<<1, 256, 0, s>>>(npairs, e_pair, E);
     count_launch();
@@ -197,8 +211,8 @@ cudaError_t scatter_pairs(int o, int v, int a_lo, int a_hi, const double* Rc, do
 {
     const int ntile = (v + T - 1) / T;
     const int ntile_a = (a_hi - a_lo + T - 1) / T;
-    const int np = o * (o + 1) / 2;
-    scatter_pairs_kernel<<<dim3(ntile_a * ntile, np), dim3(T, TR), 0, s>>>(o, v, a_lo, a_hi, Rc, R, accumulate);
+    const long long np = (long long)o * (o + 1) / 2;
+    scatter_pairs_kernel<<<batch_grid(ntile_a * ntile, np), dim3(T, TR), 0, s>>>(o, v, a_lo, a_hi, Rc, R, accumulate);
     count_launch();
     return cudaGetLastError();
 }
@@ -219,7 +233,7 @@ cudaError_t transpose_last2(long long batch, int v, const double* X, double* Y, 
 cudaError_t add_pair_swap(int o, int v, const double* X, double* Y, int alpha, cudaStream_t s)
 {
     const int ntile = (v + T - 1) / T;
-    add_pair_swap_kernel<<<dim3(ntile * ntile, o * o), dim3(T, TR), 0, s>>>(o, v, X, Y, alpha);
+    add_pair_swap_kernel<<<batch_grid(ntile * ntile, (long long)o * o), dim3(T, TR), 0, s>>>(o, v, X, Y, alpha);
     count_launch();
     return cudaGetLastError();
 }

@@ -145,7 +145,7 @@ __device__ __forceinline__ double pm_value(double x1, double x2, bool diag, int 
 // 3 = FP64 copy.
 __global__ void pm_f64_kernel(const double* __restrict__ X0, const long long* __restrict__ rowtab, long long rowmul,
                               int v, int sign, double h, int kind, int s, int beta, void* __restrict__ D,
-                              long long pitch, long long rows, int* __restrict__ e_out)
+                              long long pitch, long long rows, int* __restrict__ e_out, int* __restrict__ status)
 {
     __shared__ double S1[TT][TT + 1], S2[TT][TT + 1];
     __shared__ unsigned long long red[8];
@@ -191,7 +191,10 @@ __global__ void pm_f64_kernel(const double* __restrict__ X0, const long long* __
             }
         }
         if (pass == 0) {
-            e = exp_of_maxbits(block_max_u64(mx, red));
+            const unsigned long long bm = block_max_u64(mx, red);
+            e = exp_of_maxbits(bm);
+            // NaN or Inf in the row (or an overflowing sum t_cd + t_dc): flag the call
+            if (threadIdx.x == 0 && status && bm >= 0x7ff0000000000000ull) atomicOr(status, kStatusNonfinite);
         }
     }
     if (threadIdx.x == 0 && e_out) e_out[r] = e;
@@ -362,13 +365,15 @@ __global__ void fill_pairs_kernel(int o, int v, int strict, long long* __restric
 }  // namespace
 
 cudaError_t pm_split_f64(const double* X, const long long* rowtab, long long rowmul, long long rows, int v, int sign,
-                         double h, int kind, int s, int beta, void* D, long long pitch, int* e, cudaStream_t st)
+                         double h, int kind, int s, int beta, void* D, long long pitch, int* e, int* status,
+                         cudaStream_t st)
 {
     if (rows <= 0) return cudaSuccess;
     if (v < 1 || (sign < 0 && v < 2)) return cudaErrorInvalidValue;
     if (kind == 0 && (s < 1 || s > 8 || beta < 2 || beta > 9 || beta * s > 62)) return cudaErrorInvalidValue;
     if (rows > 0x7fffffffll) return cudaErrorInvalidValue;
-    pm_f64_kernel<<<(unsigned)rows, 256, 0, st>>>(X, rowtab, rowmul, v, sign, h, kind, s, beta, D, pitch, rows, e);
+    pm_f64_kernel<<<(unsigned)rows, 256, 0, st>>>(X, rowtab, rowmul, v, sign, h, kind, s, beta, D, pitch, rows, e,
+                                                   status);
     count_launch();
     return cudaGetLastError();
 }

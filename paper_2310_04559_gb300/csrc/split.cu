@@ -21,6 +21,7 @@
 // through a shared-memory transpose.
 #include <cuda_bf16.h>
 
+#include <algorithm>
 #include <climits>
 
 #include "cc_internal.cuh"
@@ -29,6 +30,7 @@ namespace cc {
 namespace {
 
 constexpr unsigned long long kAbsMask = 0x7fffffffffffffffull;
+constexpr unsigned long long kInfBits = 0x7ff0000000000000ull;  // |x| bit patterns >= this are Inf or NaN
 
 // Exponent e with max|row| < 2^e from the largest |x| bit pattern (0 for a zero row).
 __device__ __forceinline__ int row_exponent(unsigned long long maxbits)
@@ -83,7 +85,7 @@ __device__ __forceinline__ void digits_bf16(long long X, int s, int beta, __nv_b
 
 template <int TPR>  // threads per row: 256 (one CTA per row) or 32 (one warp per row)
 __global__ void split_rows_kernel(const RowSrc src, int s, int beta, __nv_bfloat16* __restrict__ D, long long pitch,
-                                  int* __restrict__ e_out)
+                                  int* __restrict__ e_out, int* __restrict__ status)
 {
     __shared__ unsigned long long red[256];
     const int lane = threadIdx.x % TPR;
@@ -123,7 +125,10 @@ __global__ void split_rows_kernel(const RowSrc src, int s, int beta, __nv_bfloat
     }
     if (!live) return;
     const int e = row_exponent(mx);
-    if (lane == 0) e_out[r] = e;
+    if (lane == 0) {
+        e_out[r] = e;
+        if (status && mx >= kInfBits) atomicOr(status, kStatusNonfinite);
+    }
     const int total = beta * s;
     for (long long k = lane; k < K; k += TPR)
         digits_bf16(fixed_point(X[map2(src.km, k)], e, total), s, beta, Dr + k, slice_stride);
@@ -136,19 +141,23 @@ __device__ __forceinline__ long long col_off(const ColSrc& s, long long r)
 }
 
 // Column-source max: mx[r] = max_k |X[r + k*ldk]| (bit pattern), atomically over k-chunks.
-__global__ void col_max_kernel(const ColSrc src, long long kchunk, unsigned long long* __restrict__ mx)
+__global__ void col_max_kernel(const ColSrc src, long long kchunk, unsigned long long* __restrict__ mx,
+                               int* __restrict__ status)
 {
     const long long r = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (r >= src.rows) return;
-    const long long k0 = (long long)blockIdx.y * kchunk;
-    const long long k1 = min(src.K, k0 + kchunk);
     const long long roff = col_off(src, r);
     unsigned long long m = 0;
-    for (long long k = k0; k < k1; ++k) {
-        const unsigned long long b = (unsigned long long)__double_as_longlong(src.X[roff + k * src.ldk]) & kAbsMask;
-        m = b > m ? b : m;
+    // chunks blockIdx.y, blockIdx.y + gridDim.y, ... (gridDim.y is capped at 65535)
+    for (long long k0 = (long long)blockIdx.y * kchunk; k0 < src.K; k0 += (long long)gridDim.y * kchunk) {
+        const long long k1 = min(src.K, k0 + kchunk);
+        for (long long k = k0; k < k1; ++k) {
+            const unsigned long long b = (unsigned long long)__double_as_longlong(src.X[roff + k * src.ldk]) & kAbsMask;
+            m = b > m ? b : m;
+        }
     }
     if (m) atomicMax(mx + r, m);
+    if (status && m >= kInfBits) atomicOr(status, kStatusNonfinite);
 }
 
 constexpr int CT_R = 32, CT_K = 32;  // transpose tile: 32 rows x 32 k
@@ -160,27 +169,30 @@ __global__ void split_cols_kernel(const ColSrc src, int s, int beta, const unsig
 {
     __shared__ double S[CT_K][CT_R + 1];
     const long long r0 = (long long)blockIdx.x * CT_R;
-    const long long k0 = (long long)blockIdx.y * CT_K;
     const int tx = threadIdx.x, ty = threadIdx.y;  // 32 x 8
-    for (int y = ty; y < CT_K; y += 8) {
-        const long long k = k0 + y, r = r0 + tx;
-        S[y][tx] = (k < src.K && r < src.rows) ? src.X[col_off(src, r) + k * src.ldk] : 0.0;
-    }
-    __syncthreads();
     const long long slice_stride = src.rows * pitch;
-    for (int y = ty; y < CT_R; y += 8) {
-        const long long r = r0 + y, k = k0 + tx;
-        if (r >= src.rows || k >= src.K) continue;
-        const double x = S[tx][y];
-        __nv_bfloat16* out = D + r * pitch + k;
-        if (s == 0) {
-            out[0] = __double2bfloat16(x);
-            if (k == 0) e_out[r] = 0;
-            continue;
+    // k tiles blockIdx.y, blockIdx.y + gridDim.y, ... (gridDim.y is capped at 65535)
+    for (long long k0 = (long long)blockIdx.y * CT_K; k0 < src.K; k0 += (long long)gridDim.y * CT_K) {
+        __syncthreads();
+        for (int y = ty; y < CT_K; y += 8) {
+            const long long k = k0 + y, r = r0 + tx;
+            S[y][tx] = (k < src.K && r < src.rows) ? src.X[col_off(src, r) + k * src.ldk] : 0.0;
         }
-        const int e = row_exponent(mx[r]);
-        if (k == 0) e_out[r] = e;
-        digits_bf16(fixed_point(x, e, beta * s), s, beta, out, slice_stride);
+        __syncthreads();
+        for (int y = ty; y < CT_R; y += 8) {
+            const long long r = r0 + y, k = k0 + tx;
+            if (r >= src.rows || k >= src.K) continue;
+            const double x = S[tx][y];
+            __nv_bfloat16* out = D + r * pitch + k;
+            if (s == 0) {
+                out[0] = __double2bfloat16(x);
+                if (k == 0) e_out[r] = 0;
+                continue;
+            }
+            const int e = row_exponent(mx[r]);
+            if (k == 0) e_out[r] = e;
+            digits_bf16(fixed_point(x, e, beta * s), s, beta, out, slice_stride);
+        }
     }
 }
 
@@ -265,36 +277,40 @@ __global__ void convert_cols_tf32_kernel(const ColSrc src, float* __restrict__ D
 {
     __shared__ double S[CT_K][CT_R + 1];
     const long long r0 = (long long)blockIdx.x * CT_R;
-    const long long k0 = (long long)blockIdx.y * CT_K;
     const int tx = threadIdx.x, ty = threadIdx.y;
-    for (int y = ty; y < CT_K; y += 8) {
-        const long long k = k0 + y, r = r0 + tx;
-        S[y][tx] = (k < src.K && r < src.rows) ? src.X[col_off(src, r) + k * src.ldk] : 0.0;
-    }
-    __syncthreads();
-    for (int y = ty; y < CT_R; y += 8) {
-        const long long r = r0 + y, k = k0 + tx;
-        if (r < src.rows && k < src.K) D[r * pitch + k] = to_tf32(S[tx][y]);
+    for (long long k0 = (long long)blockIdx.y * CT_K; k0 < src.K; k0 += (long long)gridDim.y * CT_K) {
+        __syncthreads();
+        for (int y = ty; y < CT_K; y += 8) {
+            const long long k = k0 + y, r = r0 + tx;
+            S[y][tx] = (k < src.K && r < src.rows) ? src.X[col_off(src, r) + k * src.ldk] : 0.0;
+        }
+        __syncthreads();
+        for (int y = ty; y < CT_R; y += 8) {
+            const long long r = r0 + y, k = k0 + tx;
+            if (r < src.rows && k < src.K) D[r * pitch + k] = to_tf32(S[tx][y]);
+        }
     }
 }
 
 }  // namespace
 
-cudaError_t split_rows_bf16(const RowSrc& src, int s, int beta, void* D, long long pitch, int* e, cudaStream_t st)
+cudaError_t split_rows_bf16(const RowSrc& src, int s, int beta, void* D, long long pitch, int* e, int* status,
+                            cudaStream_t st)
 {
     if (src.rows <= 0) return cudaSuccess;
     if (s < 0 || s > 8 || (s > 0 && (beta < 2 || beta > 9 || beta * s > 62))) return cudaErrorInvalidValue;
     if (src.K >= 4096) {
-        split_rows_kernel<256><<<(unsigned)src.rows, 256, 0, st>>>(src, s, beta, (__nv_bfloat16*)D, pitch, e);
+        split_rows_kernel<256><<<(unsigned)src.rows, 256, 0, st>>>(src, s, beta, (__nv_bfloat16*)D, pitch, e, status);
     } else {
-        split_rows_kernel<32><<<(unsigned)((src.rows + 7) / 8), 256, 0, st>>>(src, s, beta, (__nv_bfloat16*)D, pitch, e);
+        split_rows_kernel<32><<<(unsigned)((src.rows + 7) / 8), 256, 0, st>>>(src, s, beta, (__nv_bfloat16*)D, pitch, e,
+                                                                             status);
     }
     count_launch();
     return cudaGetLastError();
 }
 
 cudaError_t split_cols_bf16(const ColSrc& src, int s, int beta, void* D, long long pitch, int* e,
-                            unsigned long long* scratch_max, cudaStream_t st)
+                            unsigned long long* scratch_max, int* status, cudaStream_t st)
 {
     if (src.rows <= 0) return cudaSuccess;
     if (s < 0 || s > 8 || (s > 0 && (beta < 2 || beta > 9 || beta * s > 62))) return cudaErrorInvalidValue;
@@ -302,11 +318,11 @@ cudaError_t split_cols_bf16(const ColSrc& src, int s, int beta, void* D, long lo
         cudaError_t err = cudaMemsetAsync(scratch_max, 0, sizeof(unsigned long long) * src.rows, st);
         if (err != cudaSuccess) return err;
         const long long kchunk = 256;
-        dim3 g((unsigned)((src.rows + 255) / 256), (unsigned)((src.K + kchunk - 1) / kchunk));
-        col_max_kernel<<<g, 256, 0, st>>>(src, kchunk, scratch_max);
+        dim3 g((unsigned)((src.rows + 255) / 256), (unsigned)std::min(65535ll, (src.K + kchunk - 1) / kchunk));
+        col_max_kernel<<<g, 256, 0, st>>>(src, kchunk, scratch_max, status);
         count_launch();
     }
-    dim3 g2((unsigned)((src.rows + CT_R - 1) / CT_R), (unsigned)((src.K + CT_K - 1) / CT_K));
+    dim3 g2((unsigned)((src.rows + CT_R - 1) / CT_R), (unsigned)std::min(65535ll, (src.K + CT_K - 1) / CT_K));
     split_cols_kernel<<<g2, dim3(32, 8), 0, st>>>(src, s, beta, scratch_max, (__nv_bfloat16*)D, pitch, e);
     count_launch();
     return cudaGetLastError();
@@ -340,7 +356,7 @@ cudaError_t convert_rows_tf32(const RowSrc& src, float* D, long long pitch, cuda
 cudaError_t convert_cols_tf32(const ColSrc& src, float* D, long long pitch, cudaStream_t st)
 {
     if (src.rows <= 0) return cudaSuccess;
-    dim3 g2((unsigned)((src.rows + CT_R - 1) / CT_R), (unsigned)((src.K + CT_K - 1) / CT_K));
+    dim3 g2((unsigned)((src.rows + CT_R - 1) / CT_R), (unsigned)std::min(65535ll, (src.K + CT_K - 1) / CT_K));
     convert_cols_tf32_kernel<<<g2, dim3(32, 8), 0, st>>>(src, D, pitch);
     count_launch();
     return cudaGetLastError();

@@ -22,7 +22,8 @@ from __future__ import annotations
 
 import numpy as np
 
-__all__ = ["cholesky_vectors", "amplitudes", "cholesky_ov", "cotangent", "ladder_inputs", "WORKLOADS"]
+__all__ = ["cholesky_vectors", "amplitudes", "cholesky_ov", "cotangent", "ladder_inputs", "ladder_inputs_torch",
+           "WORKLOADS"]
 
 # Named workloads (o occupied, v virtual, n Cholesky vectors).  The paper's
 # synthetic shapes (Section 6.2, Table 1) use n = 5K, v = int(3K/4), o = K - v;
@@ -82,3 +83,20 @@ def ladder_inputs(o: int, v: int, n: int, seed: int = 0, symmetric: bool = True)
     L = cholesky_vectors(n, v, symmetric=symmetric, rng=rng)
     t2 = amplitudes(o, v, symmetric=symmetric, rng=rng)
     return L, t2
+
+
+def ladder_inputs_torch(o: int, v: int, n: int, seed: int = 0, device="cuda"):
+    """(L, t2) by the same recipe, drawn with torch's generator on `device` (for workloads whose
+    host-side generation would take minutes, e.g. o = 60, v = 600, n = 3000).  The numbers differ
+    from ladder_inputs' for the same seed; the distributions and symmetries are the same."""
+    import torch
+
+    g = torch.Generator(device=device).manual_seed(seed)
+    L = torch.randn((n, v, v), generator=g, dtype=torch.float64, device=device)
+    iu = torch.triu_indices(v, v, 1, device=device)
+    L[:, iu[1], iu[0]] = L[:, iu[0], iu[1]]
+    L *= torch.exp(-5.0 * torch.arange(n, dtype=torch.float64, device=device) / max(n, 1))[:, None, None]
+    x = torch.randn((o, o, v, v), generator=g, dtype=torch.float64, device=device).mul_(1e-2)
+    t2 = x.permute(1, 0, 3, 2).contiguous().add_(x).mul_(0.5)
+    del x
+    return L.contiguous(), t2

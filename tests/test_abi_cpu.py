@@ -34,8 +34,8 @@ def test_exports_every_declared_symbol(lib):
 
 def test_version_and_strerror(lib):
     assert b"sm_103a" in lib.cc_ladder_version()
-    for code in range(-10, 1):
-        assert lib.cc_ladder_strerror(code)
+    for code in range(-11, 1):
+        assert lib.cc_ladder_strerror(code) != b"unknown status"
     assert lib.cc_ladder_strerror(-99) == b"unknown status"
 
 
@@ -185,3 +185,26 @@ def test_binding_refuses_cpu_tensors(lib):
         Ld.workspace_size(o, v, n, mode="fp16")
     with pytest.raises(ValueError, match="unknown order"):
         Ld.plan(o, v, n, order="sideways")
+
+
+def test_probe_and_partition_argument_errors(lib):
+    out = ctypes.c_double()
+    assert lib.cc_ladder_peak_probe(0, 10, None, ctypes.byref(out)) == -9   # unknown probe
+    assert lib.cc_ladder_peak_probe(5, 10, None, ctypes.byref(out)) == -9
+    assert lib.cc_ladder_peak_probe(1, 0, None, ctypes.byref(out)) == -9    # no iterations
+    assert lib.cc_ladder_peak_probe(1, 10, None, None) == -2
+    bounds = (ctypes.c_int * 5)()
+    a = _args()
+    assert lib.cc_ladder_partition(ctypes.byref(a), 4, None) == -2
+    assert lib.cc_ladder_partition(ctypes.byref(a), 0, bounds) == -9
+    assert lib.cc_ladder_partition(ctypes.byref(a), 25, bounds) == -9      # more parts than v = 24
+    assert lib.cc_ladder_partition(ctypes.byref(a), 4, bounds) == 0
+    assert list(bounds) == [0, 6, 12, 18, 24]
+
+
+def test_energy_shape_limits(lib):
+    x = _fake(0x10000)
+    # o beyond the library's pair-count limit is a shape error, before anything is enqueued
+    assert lib.cc_ladder_energy(46341, 2, x, x, x, None, _fake(0x20000), 1 << 40, None) == -1
+    assert lib.cc_ladder_energy_noalloc(46341, 2, x, x, x, None, None) == -1
+    assert lib.cc_ladder_energy_noalloc(2, 0, x, x, x, None, None) == -1

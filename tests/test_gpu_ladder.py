@@ -302,21 +302,37 @@ def test_adjoint_workload_o16_v160_n800(dev, oracle):
 
 
 @pytest.mark.parametrize("mode", ["fp64", "ozaki_bf16"])
-def test_a_range_shards_assemble(dev, mode):
-    """Disjoint a-ranges (one per device in a multi-GPU run) write disjoint entries;
-    their sum is the full R, with and without pair symmetry."""
+def test_a_range_shards_assemble(dev, oracle, mode):
+    """Disjoint a-ranges (one per device in a multi-GPU run, from the work-balanced partition that
+    bench.py uses) write disjoint entries; their sum is the full R, with and without pair
+    symmetry, and on the pair-symmetric path the ranges' energy shares add up to the energy."""
     o, v, n = 4, 45, 70
     L, t2 = synth.ladder_inputs(o, v, n, seed=12)
     Lg, tg = cu(L, dev), cu(t2, dev)
+    R_ref = oracle.ladder(L, t2)
     for sym in (False, True):
         full = B.ladder_forward(Lg, tg, mode=mode, symmetric=sym)
+        bounds = B.partition(o, v, n, 3, mode=mode, symmetric=sym)
+        assert bounds[0] == 0 and bounds[-1] == v
         parts = torch.zeros_like(full)
-        for lo, hi in [(0, 13), (13, 30), (30, 45)]:
+        e_sum = 0.0
+        for g in range(3):
+            lo, hi = bounds[g], bounds[g + 1]
             Rp = torch.zeros_like(full)
-            B.ladder_forward(Lg, tg, R=Rp, mode=mode, symmetric=sym, a_range=(lo, hi))
+            if sym:
+                _, Eg = B.ladder_forward(Lg, tg, R=Rp, mode=mode, symmetric=sym, a_range=(lo, hi), energy=True)
+                e_g = float(Eg)
+                assert abs(e_g - oracle.energy_range(R_ref, t2, lo, hi)) <= TOL[mode] * abs(oracle.energy(R_ref, t2))
+                e_sum += e_g
+            else:
+                B.ladder_forward(Lg, tg, R=Rp, mode=mode, symmetric=sym, a_range=(lo, hi))
             # nothing outside this range's share is written
             parts += Rp
         assert rel(parts.cpu().numpy(), full.cpu().numpy()) < 1e-14
+        assert rel(parts.cpu().numpy(), R_ref) < TOL[mode]
+        if sym:
+            E = oracle.energy(R_ref, t2)
+            assert abs(e_sum - E) <= TOL[mode] * abs(E)
 
 
 @pytest.mark.parametrize("n", [7000, 20000])

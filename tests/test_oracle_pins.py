@@ -212,6 +212,28 @@ def test_energy_hand_and_identities(oracle):
     assert abs(np.vdot(R.transpose(0, 1, 3, 2), t2) - np.vdot(R.transpose(1, 0, 2, 3), t2)) < 1e-13 * abs(E)
 
 
+def test_energy_range_shares(oracle):
+    """One part's share of E under an `a`-range partition: the terms with min(a, b) in [lo, hi).
+    Pinned by hand for o = 1, v = 2, by the full range, and by additivity over a partition."""
+    R = np.array([[[[1.0, 2.0], [3.0, 5.0]]]])
+    t2 = np.array([[[[7.0, 11.0], [13.0, 17.0]]]])
+    # min(a, b) = 0: (a, b) = (0,0), (0,1), (1,0);  min = 1: (1,1) only
+    e0 = (2 * 1 - 1) * 7 + (2 * 2 - 3) * 11 + (2 * 3 - 2) * 13
+    e1 = (2 * 5 - 5) * 17
+    assert oracle.energy_range(R, t2, 0, 1) == e0
+    assert oracle.energy_range(R, t2, 1, 2) == e1
+    assert oracle.energy_range(R, t2, 0, 2) == oracle.energy(R, t2) == e0 + e1
+    o, v, n = 3, 9, 7
+    L, t2 = synth.ladder_inputs(o, v, n, seed=29)
+    R = oracle.ladder(L, t2)
+    E = oracle.energy(R, t2)
+    assert abs(oracle.energy_range(R, t2, 0, v) - E) <= 1e-14 * abs(E)
+    for cuts in ([0, 4, 9], [0, 1, 2, 5, 9], [0, 8, 9]):
+        parts = sum(oracle.energy_range(R, t2, cuts[g], cuts[g + 1]) for g in range(len(cuts) - 1))
+        assert abs(parts - E) <= 1e-13 * abs(E), cuts
+    assert oracle.energy_range(R, t2, 3, 3) == 0.0
+
+
 # --------------------------------------------------------------- gradient
 def test_gradient_identities_and_fd(oracle):
     o, v, n = 2, 5, 4
