@@ -101,13 +101,23 @@ enum cc_flags {
                                    R[i,j,a,b] = sum_cd (sum_P L_Pad L_Pbc) t2[i,j,c,d]                */
     CC_FLAG_NO_STATUS_SYNC = 8, /* do not synchronise the stream at the end; device-side failures are
                                    then reported by cc_ladder_device_status()                         */
-    CC_FLAG_HOST_T2R = 16       /* t2 and R are page-locked HOST memory (cudaHostAlloc / cudaHostRegister,
+    CC_FLAG_HOST_T2R = 16,      /* t2 and R are page-locked HOST memory (cudaHostAlloc / cudaHostRegister,
                                    addressable from the device); L, energy and the workspace stay on the
                                    device.  The kernels read t2 and write R over the host link, so
                                    o^2 v^2 may exceed device memory: the device holds one block of
                                    pairs (i <= j) at a time.  Needs CC_FLAG_SYMMETRIC_T and the
                                    integral-first order, not CC_FLAG_EXCHANGE (else CC_ERR_UNSUPPORTED);
                                    CC_ERR_ARG if t2 or R is not page-locked host memory.              */
+    CC_FLAG_HOST_L = 32         /* L is page-locked HOST memory: the library copies it to the device in
+                                   chunks of chol_chunk Cholesky vectors (the batches over the Cholesky
+                                   index of Section 5), double-buffered on a stream of its own so that
+                                   the copy of chunk q + 1 overlaps the split and integral GEMM of
+                                   chunk q; the integrals of a block are summed over the chunks.  L is
+                                   read once for the emulated mode's row scales and once per block of
+                                   `a`, so n_chol v^2 may exceed device memory.  Needs
+                                   CC_FLAG_SYMMETRIC_T and the integral-first order (else
+                                   CC_ERR_UNSUPPORTED); combines with CC_FLAG_HOST_T2R; CC_ERR_ARG if
+                                   L is not page-locked host memory.  Forward only.                    */
 };
 
 /* Full argument block for cc_ladder_fwd_ex / cc_ladder_workspace_size_ex. */
@@ -140,6 +150,9 @@ typedef struct cc_ladder_args {
                               disjoint ranges write disjoint entries, so ranges spread over
                               devices (each R zeroed first) assemble R by a sum
                               (cc_ladder_partition balances the ranges' work).                   */
+    int chol_chunk;        /* CC_FLAG_HOST_L: Cholesky vectors per streamed chunk of L (0 = planner's
+                              choice: two chunks and their slices in about an eighth of the budget,
+                              halved until the plan fits); ignored otherwise                       */
 } cc_ladder_args;
 
 /* What the planner decided for a call (for reporting and tests). */

@@ -19,7 +19,7 @@ STATUS = {
 }
 MODES = {"fp64": 0, "ozaki_bf16": 1, "ozaki_int8": 2, "tf32": 3, "bf16": 4}
 ORDERS = {"auto": 0, "integral_first": 1, "cholesky_first": 2}
-FLAG_ACCUMULATE, FLAG_SYMMETRIC_T, FLAG_EXCHANGE, FLAG_NO_STATUS_SYNC, FLAG_HOST_T2R = 1, 2, 4, 8, 16
+FLAG_ACCUMULATE, FLAG_SYMMETRIC_T, FLAG_EXCHANGE, FLAG_NO_STATUS_SYNC, FLAG_HOST_T2R, FLAG_HOST_L = 1, 2, 4, 8, 16, 32
 
 _vp = ctypes.c_void_p
 _sz = ctypes.c_size_t
@@ -33,7 +33,7 @@ class Args(ctypes.Structure):
         ("L", _vp), ("t2", _vp), ("R", _vp), ("energy", _vp),
         ("mode", _i), ("order", _i), ("a_block", _i), ("flags", _i), ("slices", _i),
         ("workspace", _vp), ("ws_bytes", _sz), ("budget_bytes", _sz), ("stream", _vp),
-        ("a_lo", _i), ("a_hi", _i),
+        ("a_lo", _i), ("a_hi", _i), ("chol_chunk", _i),
     ]
 
 

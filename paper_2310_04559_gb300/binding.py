@@ -34,10 +34,10 @@ def _order(o) -> int:
     return _lib.ORDERS[o]
 
 
-def _flags(symmetric=False, exchange=False, accumulate=False, no_sync=False, host_t2r=False) -> int:
+def _flags(symmetric=False, exchange=False, accumulate=False, no_sync=False, host_t2r=False, host_L=False) -> int:
     return ((_lib.FLAG_SYMMETRIC_T if symmetric else 0) | (_lib.FLAG_EXCHANGE if exchange else 0)
             | (_lib.FLAG_ACCUMULATE if accumulate else 0) | (_lib.FLAG_NO_STATUS_SYNC if no_sync else 0)
-            | (_lib.FLAG_HOST_T2R if host_t2r else 0))
+            | (_lib.FLAG_HOST_T2R if host_t2r else 0) | (_lib.FLAG_HOST_L if host_L else 0))
 
 
 def _check_tensor(x: torch.Tensor, name: str, shape):
@@ -75,14 +75,16 @@ def _shapes(L, t2):
 
 
 def make_args(o, v, n, mode="fp64", order="auto", symmetric=False, exchange=False, accumulate=False,
-              a_block=0, slices=0, budget=0, no_sync=False, a_range=None, host_t2r=False) -> _lib.Args:
+              a_block=0, slices=0, budget=0, no_sync=False, a_range=None, host_t2r=False, host_L=False,
+              chol_chunk=0) -> _lib.Args:
     a = _lib.Args()
     if a_range is not None:
         a.a_lo, a.a_hi = int(a_range[0]), int(a_range[1])
+    a.chol_chunk = int(chol_chunk)
     a.o, a.v, a.n_chol = o, v, n
     a.mode, a.order = _mode(mode), _order(order)
     a.a_block, a.slices = int(a_block), int(slices)
-    a.flags = _flags(symmetric, exchange, accumulate, no_sync, host_t2r)
+    a.flags = _flags(symmetric, exchange, accumulate, no_sync, host_t2r, host_L)
     a.budget_bytes = int(budget)
     return a
 
@@ -150,39 +152,45 @@ def alloc_workspace(nbytes: int, device) -> torch.Tensor:
 
 def _check_host_tensor(x: torch.Tensor, name: str, shape):
     if not isinstance(x, torch.Tensor) or x.device.type != "cpu" or not x.is_pinned():
-        raise ValueError(f"{name} must be a page-locked CPU tensor (tensor.pin_memory()) with host_t2r=True")
+        raise ValueError(f"{name} must be a page-locked CPU tensor (tensor.pin_memory()) with host_t2r / host_L")
     if x.dtype != torch.float64 or tuple(x.shape) != tuple(shape) or not x.is_contiguous():
         raise ValueError(f"{name} must be contiguous float64 of shape {tuple(shape)}")
 
 
 def ladder_forward(L, t2, R=None, mode="ozaki_bf16", order="auto", symmetric=False, exchange=False,
                    accumulate=False, a_block=0, slices=0, energy=False, workspace=None, budget=0, no_sync=False,
-                   a_range=None, host_t2r=False):
+                   a_range=None, host_t2r=False, host_L=False, chol_chunk=0, device=None):
     """R (new tensor unless given) and optionally the pair energy E (0-d tensor).
     a_range=(lo, hi) computes only the columns a in [lo, hi) (see cc_ladder_args).
     host_t2r=True: t2 and R are page-locked CPU tensors read and written over the host link
-    (problems whose o^2 v^2 exceeds device memory); needs symmetric=True."""
+    (problems whose o^2 v^2 exceeds device memory); needs symmetric=True.
+    host_L=True: L is a page-locked CPU tensor streamed to the device in chunks of chol_chunk
+    Cholesky vectors (problems whose n_chol v^2 exceeds device memory); needs symmetric=True.
+    device: the GPU when no argument lives there (host_L with host_t2r; default: the current one)."""
     lib = _lib.load()
     o, v, n = _shapes(L, t2)
-    _check_tensor(L, "L", (n, v, v))
+    (_check_host_tensor if host_L else _check_tensor)(L, "L", (n, v, v))
     check = _check_host_tensor if host_t2r else _check_tensor
     check(t2, "t2", (o, o, v, v))
+    if device is None:
+        gpu = [x.device for x in (L, t2) if x.device.type == "cuda"]
+        device = gpu[0] if gpu else torch.device("cuda", torch.cuda.current_device())
     if R is None:
         R = torch.empty_like(t2) if not accumulate else torch.zeros_like(t2)
         if host_t2r:
             R = R.pin_memory()
     check(R, "R", (o, o, v, v))
     a = make_args(o, v, n, mode, order, symmetric, exchange, accumulate, a_block, slices, budget, no_sync, a_range,
-                  host_t2r)
+                  host_t2r, host_L, chol_chunk)
     if workspace is None:
         ws = ctypes.c_size_t()
         _lib.check(lib.cc_ladder_workspace_size_ex(ctypes.byref(a), ctypes.byref(ws)), "cc_ladder_workspace_size_ex")
-        workspace = alloc_workspace(ws.value, L.device)
+        workspace = alloc_workspace(ws.value, device)
     _same_device(L, t2, R, workspace)
-    E = torch.empty((), dtype=torch.float64, device=L.device) if energy else None
+    E = torch.empty((), dtype=torch.float64, device=device) if energy else None
     a.L, a.t2, a.R, a.energy = _ptr(L), _ptr(t2), _ptr(R), _ptr(E)
     a.workspace, a.ws_bytes = _ptr(workspace), workspace.numel()
-    a.stream = _stream(L.device)
+    a.stream = _stream(device)
     _lib.check(lib.cc_ladder_fwd_ex(ctypes.byref(a)), "cc_ladder_fwd_ex")
     return (R, E) if energy else R
 

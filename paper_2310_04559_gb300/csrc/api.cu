@@ -48,12 +48,6 @@ constexpr int kDefaultSlices = 6;
 constexpr int kBeta = 7;                 // bits per Ozaki slice (balanced digits in [-64, 64])
 constexpr int kMixedChunk = 16384;       // K elements per FP32 accumulation in the BF16 / TF32 modes
 constexpr int kFixF = 26;                // fixed-point fraction bits (of a level-0 unit) in the Ozaki epilogue
-// Longest contraction one FP32 level sum covers in an integral build (A and B rows from the same
-// Cholesky vectors).  In a diagonal integral (ac|ac) the square of a lower digit, nearly uniform on
-// [-64, 63], adds with one sign at every P: about 1365 per term, so a level sum would pass 2^24
-// (the end of exact FP32 integers) after about 12 000 terms.  Longer K is split across CTAs
-// whose exact int64 partials are added, which keeps every level sum near 2^23.
-constexpr int kExactK = 6144;
 constexpr int kFixedBase = 2 - 2 * kBeta - kFixF;  // exponent of one fixed-point unit, before row/col exponents
 constexpr size_t kDefaultBudget = 150ull << 30;
 
@@ -86,6 +80,8 @@ struct Ctx {
     long long Kp, Km; // packed path: v(v+1)/2 and v(v-1)/2
     bool host;        // t2 and R are page-locked host memory, read and written over the host link
     long long PB;     // packed path: pairs (i <= j) per pair block (o(o+1)/2 unless host)
+    bool hostL;       // L is page-locked host memory, streamed to the device in chunks of Cholesky vectors
+    long long PC;     // hostL: Cholesky vectors per chunk (n otherwise)
     int* status = nullptr;  // device status word of the call (the splits flag non-finite inputs there)
 };
 
@@ -112,7 +108,7 @@ struct FwdLayout {
     // packed path
     size_t pairtab_m, rtab, Tp, eTp, Tm, eTm, Vp, eVp, Vm, eVm, Rpc, Rmc;
     // integral-first
-    size_t V, Lw, eL, colmax, tw, et, Vw, eV;
+    size_t V, Lw, eL, colmax, tw, et, Vw, eV, Lraw;
     // Cholesky-first
     size_t X2, LwA, eLA, twB, etB, X2w, eX2, LwB, eLB;
     size_t total;
@@ -134,8 +130,10 @@ FwdLayout layout_packed(const Ctx& c, long long P)
     L.epart = cv.take(8 * energy_scratch_doubles(c.o, c.v));
     L.epair = cv.take(8 * o * o);
     L.V = cv.take(8 * P * vv);
+    if (c.hostL) L.Lraw = cv.take(2 * 8 * c.PC * vv);  // two FP64 chunks of L: one arriving, one in use
+    const long long nk = c.hostL ? c.PC : n;           // K of the L slices held at once
     if (!f64) {
-        L.Lw = cv.take(es * s * vv * pitch_for(n, es));
+        L.Lw = cv.take(es * s * vv * pitch_for(nk, es));
         L.eL = cv.take(4 * vv);
         L.colmax = cv.take(8 * vv);
     }
@@ -285,7 +283,25 @@ long long pick_block_pb(const Ctx& c, size_t bytes, int requested, size_t* need)
 // split of their t2 rows for every integral block and shorter ladder GEMMs, so the largest pair
 // block (halving from all pairs) that leaves room for integral blocks of at least 4 `a` values
 // (or all of them) is taken; when no pair block does, the largest one that fits one `a` per block.
+long long pick_block_host(Ctx& c, size_t bytes, int requested, size_t* need);
+
+// Streamed L: the chunk of Cholesky vectors starts at the caller's chol_chunk or at the one whose
+// two FP64 buffers and slices take an eighth of the budget, and halves until a plan fits.
 long long pick_block(Ctx& c, size_t bytes, int requested, size_t* need)
+{
+    if (!c.hostL) return pick_block_host(c, bytes, requested, need);
+    const long long vv = (long long)c.v * c.v;
+    const long long per = vv * (16 + (c.mode == CC_FP64 ? 0 : esz_of(c.mode) * (long long)c.s));
+    long long pc = c.PC > 0 ? std::min<long long>(c.PC, c.n)
+                            : std::max(1ll, std::min<long long>(c.n, (long long)(bytes / 8) / per));
+    for (;; pc = (pc + 1) / 2) {
+        c.PC = pc;
+        const long long P = pick_block_host(c, bytes, requested, need);
+        if (P >= 0 || pc == 1) return P;
+    }
+}
+
+long long pick_block_host(Ctx& c, size_t bytes, int requested, size_t* need)
 {
     if (!(c.host && c.packed)) return pick_block_pb(c, bytes, requested, need);
     const long long want = (long long)std::min(c.v, 4) * c.v;
@@ -336,8 +352,9 @@ int make_ctx(const cc_ladder_args* a, Ctx* c)
     if (a->order < CC_ORDER_AUTO || a->order > CC_ORDER_CHOLESKY_FIRST) return CC_ERR_ARG;
     if (a->a_block < 0) return CC_ERR_ARG;
     if (a->flags & ~(CC_FLAG_ACCUMULATE | CC_FLAG_SYMMETRIC_T | CC_FLAG_EXCHANGE | CC_FLAG_NO_STATUS_SYNC |
-                     CC_FLAG_HOST_T2R))
+                     CC_FLAG_HOST_T2R | CC_FLAG_HOST_L))
         return CC_ERR_ARG;
+    if (a->chol_chunk < 0) return CC_ERR_ARG;
     if (a->mode == CC_OZAKI_BF16 && a->slices != 0 && (a->slices < 2 || a->slices > 8)) return CC_ERR_ARG;
     if (a->a_lo < 0 || a->a_hi < 0 || a->a_lo > a->v || a->a_hi > a->v || (a->a_hi && a->a_hi <= a->a_lo))
         return CC_ERR_ARG;
@@ -355,14 +372,17 @@ int make_ctx(const cc_ladder_args* a, Ctx* c)
     // the order's cost model sees the packed flop count
     const bool can_pack = c->sym;
     c->packed = can_pack;
-    // host-resident amplitudes stream pair blocks through the integral-first order only
-    c->order = ((a->flags & CC_FLAG_HOST_T2R) && a->order == CC_ORDER_AUTO) ? (int)CC_ORDER_INTEGRAL_FIRST
-                                                                           : pick_order(*c, a->order);
+    // host-resident amplitudes and streamed L run through the integral-first order only
+    const bool hostflags = (a->flags & (CC_FLAG_HOST_T2R | CC_FLAG_HOST_L)) != 0;
+    c->order = (hostflags && a->order == CC_ORDER_AUTO) ? (int)CC_ORDER_INTEGRAL_FIRST : pick_order(*c, a->order);
     c->packed = can_pack && c->order == CC_ORDER_INTEGRAL_FIRST;
     c->host = (a->flags & CC_FLAG_HOST_T2R) != 0;
     c->PB = c->pp;
+    c->hostL = (a->flags & CC_FLAG_HOST_L) != 0;
+    c->PC = c->hostL ? a->chol_chunk : c->n;
     // host-resident amplitudes run on the packed path only, without the exchange copy
     if (c->host && (!c->packed || c->exch)) return CC_ERR_UNSUPPORTED;
+    if (c->hostL && !c->packed) return CC_ERR_UNSUPPORTED;
     return CC_OK;
 }
 
@@ -440,8 +460,8 @@ double tc_products(const Ctx& c) { return c.mode == CC_OZAKI_BF16 ? c.s * (c.s +
 
 // Output elements of an M x N slice GEMM that lie in tiles the triangular skip keeps
 // (a(m) = m / tri, b(n) = n / tri; a tile goes when b < a for all its elements).
-// Tile edges TM x TN: 128 x 256 in gemm_tc.cu, 64 x 64 in gemm_f64.cu.
-double tri_elems(long long M, long long N, long long tri, long long TM = 128, long long TN = 256)
+// Tile edges TM x TN: 256 x 128 (a CTA pair) in gemm_tc.cu, 64 x 64 in gemm_f64.cu.
+double tri_elems(long long M, long long N, long long tri, long long TM = 256, long long TN = 128)
 {
     if (tri <= 0) return (double)M * N;
     double e = 0.0;
@@ -454,47 +474,67 @@ double tri_elems(long long M, long long N, long long tri, long long TM = 128, lo
     return e;
 }
 
+// Longest K-chunk over which the FP32 sums of the levels glo .. glo + gn - 1 stay exact for any
+// input: balanced digits are at most 2^(beta-1) in magnitude, so a level with q products per K
+// element grows by at most q 2^(2 beta - 2) per element, and below 2^24 every partial sum is an
+// exact FP32 integer.  Rounded down to whole K-steps of the GEMM (64 bf16 elements).
+int exact_chunk(int glo, int gn, int s)
+{
+    int q = 1;
+    for (int L = glo; L < glo + gn; ++L) q = std::max(q, std::min(L, s - 1) - std::max(0, L - s + 1) + 1);
+    const long long per = 1ll << (2 * kBeta - 2);
+    const long long kc = ((1ll << 24) / (q * per)) / 64 * 64;
+    return (int)std::max(64ll, kc);
+}
+
 // intermediate: the output feeds another slice GEMM through split_fixed_rows, so in
 // the emulated mode it stays int64 fixed point (no FP64 work, no loads in the epilogue).
 // tri > 0: triangular tile skip with a(m) = m / tri, b(n) = n / tri.
+// add_int64 (intermediate only): add the int64 result into the output instead of storing it
+// (later chunks of a contraction split on the host, e.g. streamed Cholesky vectors).
 int run_tc(const char* name, const Ctx& c, int M, int N, int K, const Operand& A, long long rowA0, const Operand& B,
            long long rowB0, const OutDesc& out, int* status, cudaStream_t st, bool intermediate = false,
-           long long tri = 0)
+           long long tri = 0, bool add_int64 = false)
 {
     ProfScope ps(name, st, 2.0 * tri_elems(M, N, tri) * K * tc_products(c));
+    // C = A B^T and C^T = B A^T are the same GEMM: take the orientation whose 256 x 128 pair
+    // tiles pad the output least (not with the triangular skip, which is one-sided)
+    auto padded = [](long long m, long long n) { return (double)((m + 255) / 256 * 256) * ((n + 127) / 128 * 128); };
+    const bool swap = tri == 0 && padded(N, M) < padded(M, N);
+    const Operand& Aop = swap ? B : A;
+    const Operand& Bop = swap ? A : B;
+    OutDesc o = out;
+    if (swap) std::swap(o.rmap, o.cmap);
+    if (swap) { std::swap(M, N); std::swap(rowA0, rowB0); }
     GemmTc g{};
     g.kind = c.mode == CC_TF32 ? TC_TF32 : TC_BF16;
     g.M = M; g.N = N; g.K = K;
-    g.A = A.D; g.pitchA = A.pitch; g.rowsA = A.rows; g.rowA0 = rowA0;
-    g.B = B.D; g.pitchB = B.pitch; g.rowsB = B.rows; g.rowB0 = rowB0;
+    g.A = Aop.D; g.pitchA = Aop.pitch; g.rowsA = Aop.rows; g.rowA0 = rowA0;
+    g.B = Bop.D; g.pitchB = Bop.pitch; g.rowsB = Bop.rows; g.rowB0 = rowB0;
     g.slices = c.s;
-    g.eA = c.mode == CC_TF32 ? nullptr : A.e;
-    g.eB = c.mode == CC_TF32 ? nullptr : B.e;
+    g.eA = c.mode == CC_TF32 ? nullptr : Aop.e;
+    g.eB = c.mode == CC_TF32 ? nullptr : Bop.e;
     g.beta = kBeta;
     g.scale_base = c.mode == CC_OZAKI_BF16 ? 2 - 2 * kBeta : 0;
     if (c.mode == CC_OZAKI_BF16) {
-        // levels 0 .. s-1 (all products i + j <= s-1), paired from the top
+        // levels 0 .. s-1 (all products i + j <= s-1), paired from the top; each pass covers at
+        // most exact_chunk() K elements, so every FP32 level sum is exact for any input
         g.ngroups = 0;
         for (int L = c.s - 1; L >= 0; L -= 2) {
             g.glo[g.ngroups] = L >= 1 ? L - 1 : 0;
             g.gn[g.ngroups] = L >= 1 ? 2 : 1;
-            g.gkc[g.ngroups] = 0;
+            g.gkc[g.ngroups] = exact_chunk(g.glo[g.ngroups], g.gn[g.ngroups], c.s);
             ++g.ngroups;
         }
-        g.epi = out.accumulate ? EPI_FP64_RMW : (intermediate ? EPI_FIXED64_RED : EPI_FIXED64);
+        g.epi = intermediate ? (add_int64 ? EPI_FIXED64_ADD : EPI_FIXED64_RED) : EPI_FIXED64;
         g.fixF = kFixF;
-        if (g.epi == EPI_FIXED64_RED && K > kExactK) {
-            // at most 64 splits: every split then still owns a non-empty K range
-            g.epi = EPI_FIXED64_ADD;
-            g.ksplit = (int)std::min<long long>(((long long)K + kExactK - 1) / kExactK, 64);
-        }
-        // Final outputs with few tiles: split K so the CTAs fill whole waves (int64 adds,
-        // then one conversion pass).
-        if (g.epi == EPI_FIXED64) {
-            const long long tiles = (long long)((M + 127) / 128) * ((N + 255) / 256);
-            const int nsm = device_sm_count();
+        // Few tiles of long K: split K over pairs of CTAs so that the items fill whole waves of
+        // the device (int64 adds into a zeroed output, then one conversion pass for final outputs)
+        if (!o.accumulate) {
+            const long long tiles = (long long)((M + 255) / 256) * ((N + 127) / 128);
+            const int npairs = std::max(1, device_sm_count() / 2);
             auto eff = [&](int S) {
-                const double w = (double)tiles * S / nsm;
+                const double w = (double)tiles * S / npairs;
                 return w / std::ceil(w);
             };
             int best = 1;
@@ -512,15 +552,15 @@ int run_tc(const char* name, const Ctx& c, int M, int N, int K, const Operand& A
         g.fixF = 0;
     }
     g.tri_rdiv = g.tri_cdiv = tri;
-    g.out = out;
+    g.out = o;
     g.status = status;
     g.wait_ns = g_wait_ns.load();
     if (g.epi == EPI_FIXED64_ADD) {
-        CC_CU(zero_out(M, N, out, st));
+        if (!add_int64) CC_CU(zero_out(M, N, o, st));
         CC_CU(gemm_tc(g, st));
         // an intermediate stays int64 fixed point: its consumer applies the exponents
         if (intermediate) return CC_OK;
-        return check_cuda(fixed_to_f64(M, N, out, A.e, rowA0, B.e, rowB0, kFixedBase, st));
+        return check_cuda(fixed_to_f64(M, N, o, g.eA, rowA0, g.eB, rowB0, kFixedBase, st));
     }
     return check_cuda(gemm_tc(g, st));
 }
@@ -551,10 +591,58 @@ int fwd_packed(const Ctx& c, const cc_ladder_args* a, const double* Lsrc, const 
     Tm.D = at<void>(ws, Lo.Tm); Tm.e = at<int>(ws, Lo.eTm); Tm.rows = c.pm; Tm.pitch = pitch_for(c.Km, es);
     Vp.D = at<void>(ws, Lo.Vp); Vp.e = at<int>(ws, Lo.eVp); Vp.pitch = Tp.pitch;
     Vm.D = at<void>(ws, Lo.Vm); Vm.e = at<int>(ws, Lo.eVm); Vm.pitch = Tm.pitch;
-    if (!f64) {
+    unsigned long long* colmax = at<unsigned long long>(ws, Lo.colmax);
+    // Streamed L (CC_FLAG_HOST_L): chunks of PC Cholesky vectors are copied from page-locked host
+    // memory into two device buffers on a second stream, so that chunk q + 1 arrives while chunk q
+    // is split and contracted (the batches of Cholesky vectors of Section 5, overlapped); events
+    // order every copy after the last use of its buffer.  Stream and events belong to this call.
+    struct Streamer {
+        cudaStream_t cs = nullptr;
+        cudaEvent_t copied[2] = {nullptr, nullptr}, freed[2] = {nullptr, nullptr};
+        ~Streamer()
+        {
+            for (int b = 0; b < 2; ++b) {
+                if (copied[b]) cudaEventDestroy(copied[b]);
+                if (freed[b]) cudaEventDestroy(freed[b]);
+            }
+            if (cs) cudaStreamDestroy(cs);
+        }
+    } sm;
+    double* Lraw = c.hostL ? at<double>(ws, Lo.Lraw) : nullptr;
+    if (c.hostL) {
+        CC_CU(cudaStreamCreateWithFlags(&sm.cs, cudaStreamNonBlocking));
+        for (int b = 0; b < 2; ++b) {
+            CC_CU(cudaEventCreateWithFlags(&sm.copied[b], cudaEventDisableTiming));
+            CC_CU(cudaEventCreateWithFlags(&sm.freed[b], cudaEventDisableTiming));
+        }
+    }
+    // consume(buf, P0, Pq): enqueue on st the work that reads chunk [P0, P0 + Pq) of L in buf
+    auto stream_L = [&](auto&& consume) -> int {
+        long long q = 0;
+        for (long long P0 = 0; P0 < n; P0 += c.PC, ++q) {
+            const long long Pq = std::min<long long>(c.PC, n - P0);
+            const int b = (int)(q & 1);
+            double* buf = Lraw + b * c.PC * vv;
+            if (q >= 2) CC_CU(cudaStreamWaitEvent(sm.cs, sm.freed[b], 0));
+            CC_CU(cudaMemcpyAsync(buf, Lsrc + P0 * vv, (size_t)(Pq * vv) * 8, cudaMemcpyHostToDevice, sm.cs));
+            CC_CU(cudaEventRecord(sm.copied[b], sm.cs));
+            CC_CU(cudaStreamWaitEvent(st, sm.copied[b], 0));
+            CC_TRY(consume(buf, P0, Pq));
+            CC_CU(cudaEventRecord(sm.freed[b], st));
+        }
+        return CC_OK;
+    };
+    if (!f64 && !c.hostL) {
         // L rows (a,c) are contiguous in L[P][a][c]; K = P is strided
         ColSrc ls{Lsrc, vv, vv, n, 0, plain_map(0)};
-        CC_TRY(prep_cols(c, ls, Lw, at<unsigned long long>(ws, Lo.colmax), st));
+        CC_TRY(prep_cols(c, ls, Lw, colmax, st));
+    } else if (ozaki && c.hostL) {
+        // row scales of the Ozaki split need every Cholesky vector: one streaming pass for the maxima
+        CC_CU(cudaMemsetAsync(colmax, 0, 8 * vv, st));
+        CC_TRY(stream_L([&](const double* buf, long long, long long Pq) {
+            ColSrc ls{buf, vv, vv, Pq, 0, plain_map(0)};
+            return check_cuda(cols_max(ls, colmax, c.status, st));
+        }));
     }
     // Pair blocks [q0, q1) of the i <= j pairs; their pairs i < j are [s0, s1) in the strict
     // enumeration (s(p) = p - i - [j > i] pairs i < j precede pair p = (i, j)).
@@ -588,7 +676,34 @@ int fwd_packed(const Ctx& c, const cc_ladder_args* a, const double* Lsrc, const 
         const long long nr = (long long)Ab * Nb - (long long)Ab * (Ab - 1) / 2;
         // KG1: V[al][b'][c][d] = sum_P L[P, a0+al, c] L[P, a0+b', d], tiles with b < a skipped
         OutDesc o1{V, split_map(v, (long long)Nb * vv, v), split_map(v, vv, 1), 0};
-        if (f64) {
+        if (c.hostL) {
+            // the block's integrals summed over the chunks of Cholesky vectors (additive in P)
+            CC_TRY(stream_L([&](const double* buf, long long P0, long long Pq) -> int {
+                OutDesc oq = o1;
+                if (f64) {
+                    GemmF64 g{};
+                    g.M = Ab * c.v; g.N = Nb * c.v; g.K = (int)Pq;
+                    g.A = buf; g.am = plain_map(1, (long long)a0 * v); g.ak = plain_map(vv);
+                    g.B = buf; g.bm = plain_map(1, (long long)a0 * v); g.bk = plain_map(vv);
+                    oq.accumulate = P0 > 0;
+                    g.out = oq;
+                    g.tri = v;
+                    return run_f64("kg1_f64", g, st, tri_elems(g.M, g.N, v, 64, 64));
+                }
+                ColSrc ls{buf, vv, vv, Pq, 0, plain_map(0)};
+                if (ozaki) {
+                    ProfScope ps("split", st);
+                    Lw.rows = vv;
+                    Lw.pitch = pitch_for(Pq, es);
+                    CC_CU(split_cols_bf16(ls, c.s, kBeta, Lw.D, Lw.pitch, Lw.e, colmax, c.status, st, true));
+                } else {
+                    CC_TRY(prep_cols(c, ls, Lw, colmax, st));
+                    oq.accumulate = P0 > 0;  // mixed modes: FP64 integral block
+                }
+                return run_tc("kg1_tc", c, Ab * c.v, Nb * c.v, (int)Pq, Lw, (long long)a0 * v, Lw, (long long)a0 * v,
+                              oq, status, st, true, v, ozaki && P0 > 0);
+            }));
+        } else if (f64) {
             GemmF64 g{};
             g.M = Ab * c.v; g.N = Nb * c.v; g.K = c.n;
             g.A = Lsrc; g.am = plain_map(1, (long long)a0 * v); g.ak = plain_map(vv);
@@ -655,7 +770,7 @@ int fwd_impl(const cc_ladder_args* a, const double* Lsrc_override = nullptr)
         return CC_ERR_ALIGN;
     if (is_tc(c.mode) && !tc_gemm_available()) return CC_ERR_UNSUPPORTED;
     if (c.host) {
-        // t2 and R must be page-locked host memory the device can address; L stays on the device
+        // t2 and R must be page-locked host memory the device can address
         cudaPointerAttributes pa{};
         for (const void* hp : {(const void*)a->t2, (const void*)a->R}) {
             if (cudaPointerGetAttributes(&pa, hp) != cudaSuccess || pa.type != cudaMemoryTypeHost ||
@@ -663,6 +778,14 @@ int fwd_impl(const cc_ladder_args* a, const double* Lsrc_override = nullptr)
                 cudaGetLastError();
                 return CC_ERR_ARG;
             }
+        }
+    }
+    if (c.hostL) {
+        // L must be page-locked host memory (the source of asynchronous copies)
+        cudaPointerAttributes pa{};
+        if (cudaPointerGetAttributes(&pa, Lsrc) != cudaSuccess || pa.type != cudaMemoryTypeHost) {
+            cudaGetLastError();
+            return CC_ERR_ARG;
         }
     }
     size_t need = 0;

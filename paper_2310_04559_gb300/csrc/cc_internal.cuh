@@ -121,8 +121,13 @@ struct ColSrc {
     const double* X; long long ldk; long long rows, K;
     long long brows; Map2 bmap;
 };
+// premax: scratch_max already holds every row's max |x| bit pattern (over a K range that may be
+// longer than this call's, e.g. all Cholesky vectors when L arrives in chunks): rows are split
+// with those exponents and nothing is recomputed.
 cudaError_t split_cols_bf16(const ColSrc& src, int s, int beta, void* D, long long pitch, int* e,
-                            unsigned long long* scratch_max, int* status, cudaStream_t st);
+                            unsigned long long* scratch_max, int* status, cudaStream_t st, bool premax = false);
+// mx[r] = max(mx[r], max_k |X(r, k)| as a bit pattern) (atomic; mx is not cleared).
+cudaError_t cols_max(const ColSrc& src, unsigned long long* mx, int* status, cudaStream_t st);
 // Ozaki split of an int64 fixed-point intermediate (a slice-GEMM output kept as
 // EPI_FIXED64_RED).  Row r, element k = o*inner + i is X[r*ldx + k] * 2^e with
 // e = eA[amap(r) + o] + eB[bmap(r) + i] + base.  Integer arithmetic only.

@@ -4,85 +4,99 @@
 //   C[rmap(m) + cmap(n)] (= or +=) sum_levels 2^(eA[m] + eB[n] + base - beta*level)
 //                                  * sum_{i+j=level} A_i(m,:) . B_j(n,:)
 //
-// Operands are K-major slice stacks D[slice][row][pitch].  One CTA owns a
-// 128 x 256 output tile.  The slice-product levels are processed in groups of
-// at most two (a "pass" = one group over one K-range); each level of a group
-// accumulates in FP32 in its own TMEM accumulator (2 x 256 columns), exact for
-// integer-valued slices while partial sums stay below 2^24.
+// Operands are K-major slice stacks D[slice][row][pitch].  A pair of CTAs (a
+// cluster of two SMs) owns a 256 x 128 output tile: each CTA stages its 128 rows
+// of A and 64 of the tile's 128 rows of B, and the leader CTA issues
+// tcgen05.mma.cta_group::2 (M = 256, N = 128), which reads both CTAs' shared
+// memory and accumulates 128 x 128 FP32 per CTA in its tensor memory.  The
+// kernel is persistent: every pair walks a strided list of (tile, K-split) items.
+//
+// Passes.  The slice-product levels L (products A_i B_j with i + j = L) are
+// processed in groups of at most two; a "pass" is one group over one K-chunk, and
+// each level of the pass accumulates in FP32 in its own 128-column TMEM region.
+// Two such buffers (2 x 2 x 128 = all 512 columns) alternate between passes, so
+// the epilogue drains pass p while the MMAs of pass p + 1 run.
+//
+// Exactness of the emulated mode.  Slices are balanced base-2^7 digits, |d| <= 64,
+// so one product is at most 2^12 in magnitude and a level with q products per K
+// element grows by at most q * 2^12 per element.  A pass covers at most
+// 4096 / q K elements of its levels (the host chooses the chunks), so every
+// partial FP32 sum is an integer below 2^24 and exact, whatever the input.  The
+// epilogue converts each pass exactly to a signed 64-bit fixed-point number
+// (2^-fixF of a level-0 unit; a level pair as acc_L1 * 2^beta + acc_L2) and adds
+// it to a running sum held in the epilogue threads' registers: 128 x 128 int64
+// per CTA, one row and 64 columns per thread.  The sum is written once per item:
+// scaled to FP64 (final outputs, = or +=), stored as int64 (intermediates, whose
+// consumer applies the exponents), or added with red.global (K split across pairs).
+// In the mixed modes the running sum is FP64.
 //
 // Operand reuse: for every K-step (64 bf16 / 32 tf32 elements = one 128-byte
-// swizzle atom per row) each slice tile the group needs is loaded once.  The B
-// slices stream in order j = lo..hi through a ring of 32 KB slots; the A slices
-// arrive in order i = hi..lo through a ring of 16 KB slots, so B_j meets every
-// A_i with i + j in the group while A_i lives only until its last partner
-// B_{L2-i} has passed (about two B steps).  For 6 slices the 21 slice products
-// of a K-step cost 24 tile loads instead of 42.
+// swizzle atom per row) each slice tile a pass needs is loaded once.  The B
+// slices stream in order j = lo..hi through a ring; the A slices arrive in order
+// i = hi..lo through a FIFO, so B_j meets every A_i with i + j in the pass while
+// A_i lives only until its last partner has passed.
 //
-// Epilogues:
-//   FIXED64  every pass adds its levels, converted exactly to a signed 64-bit
-//            fixed-point number (2^-F of a level-0 unit), into the output tile
-//            held as int64; the last pass scales it once into FP64.  No FP64
-//            arithmetic until that single conversion (GB300's FP64 pipe is slow).
-//   FIXED64_RED  as FIXED64 but the output stays int64 fixed point: the first pass
-//            stores, later passes add with red.global (no loads in the epilogue); the
-//            split kernel that consumes the intermediate applies the exponents.
-//   FIXED64_ADD  split-K: every pass of every CTA adds with red.global into an int64
-//            tile zeroed beforehand; fixed_to_f64 converts it afterwards.
-//   FP64RMW  every pass adds 2^e * acc into the FP64 output (mixed modes, and
-//            accumulation into caller data).  Single-level passes alternate the
-//            two accumulators so the MMAs of pass p+1 overlap the drain of pass p.
-//
-// Warp roles (352 threads): warp 0 TMA producer, warps 1-2 MMA issuers
-// (tcgen05.mma.cta_group::1, M=128, N=256; warp 1 also allocates TMEM), warps 3..10 epilogue:
-// two warps per TMEM lane quarter, each owning one half of the tile's columns (tcgen05.ld of
-// 32 lanes x 16 columns, transpose through shared memory, global accesses of two rows x 128
-// contiguous bytes per instruction).  The epilogue of a pass keeps the MMA warps waiting, so
-// it is kept short: both levels of a pair are combined into one int64 per element.  CTAs are rastered in groups of M-tiles so the
-// CTAs resident at once share their A and B tiles in L2.
+// Roles (384 threads, three warpgroups): warp 0 TMA producer (both CTAs; the
+// copies of both complete on the leader's barriers, cp.async.bulk.tensor
+// .cta_group::2), warps 1-2 MMA issuers in the leader (one per level of a pass;
+// warp 1 of each CTA allocates TMEM), warp 3 idle, warps 4-11 epilogue (two per
+// TMEM lane quarter).  setmaxnreg moves registers from warpgroup 0 to the
+// epilogue warpgroups, which hold the running sums.  No multicast instruction is
+// used: the leader signals the follower's barriers with separate commits.
 //
 // Every mbarrier wait is bounded (globaltimer); on expiry the CTA raises a
-// shared abort flag and the device status word, drains the copies and MMAs it
-// has in flight (with a fixed bound), frees TMEM and exits.
+// shared abort flag and the device status word, drains what it has in flight
+// (with a fixed bound), and both CTAs meet at the final cluster barrier, free
+// TMEM and exit.
 #include <cuda.h>
 #include <cudaTypedefs.h>
 #include <cuda_runtime.h>
 
 #include <cstdlib>
 #include <mutex>
+#include <type_traits>
 
 #include "cc_internal.cuh"
 
 namespace cc {
 namespace {
 
-constexpr int BM = 128, BN = 256;
+constexpr int BM = 128;                        // output rows per CTA (a pair covers 2 BM)
+constexpr int BN = 128;                        // output columns per pair tile
+constexpr int BNH = BN / 2;                    // B rows each CTA of a pair stages
 constexpr int ROW_BYTES = 128;                 // K bytes per tile row: one 128-byte swizzle atom
 constexpr int A_TILE = BM * ROW_BYTES;         // 16 KB per A slice tile
-constexpr int B_TILE = BN * ROW_BYTES;         // 32 KB per B slice tile
-constexpr int NA = 4, NB = 4;                  // A ring and B ring slots (powers of two)
-static_assert((NA & (NA - 1)) == 0 && (NB & (NB - 1)) == 0, "ring sizes must be powers of two");
+constexpr int B_TILE = BNH * ROW_BYTES;        // 8 KB per half B slice tile
+constexpr int NA = 8, NB = 8;                  // A FIFO and B ring slots
 constexpr int TILE_SMEM = NA * A_TILE + NB * B_TILE;  // 192 KB
 constexpr int MAX_SLICES = 8;
+constexpr int ISSUERS = 2;                     // MMA-issuing warps (one per level of a pass)
 constexpr int EPI_WARPS = 8;                   // two per TMEM lane quarter
-constexpr int ISSUERS = 2;                     // MMA-issuing warps (one per level of a pair)
-constexpr int THREADS = 32 * (1 + ISSUERS + EPI_WARPS);
-constexpr int TMEM_COLS = 512;
+constexpr int EPI_THREADS = 32 * EPI_WARPS;
+constexpr int THREADS = 32 * 4 + EPI_THREADS;  // 384
+constexpr int TMEM_COLS = 512;                 // 2 buffers x 2 levels x BN columns
+constexpr int COLS_PER_THREAD = BN / 2;        // 64 accumulator columns per epilogue thread
+// setmaxnreg split of the 384 x 168 registers of the launch: warpgroup 0 keeps 88,
+// the two epilogue warpgroups (running sums) get 208: 128 * 88 + 256 * 208 = 384 * 168.
+constexpr int REG_LAUNCH = 168, REG_LOW = 88, REG_HIGH = 208;
+static_assert(128 * REG_LOW + 256 * REG_HIGH <= THREADS * REG_LAUNCH, "register split exceeds the launch's share");
 constexpr unsigned long long kDrainLimitNs = 1000000000ull;  // bound on the abort-path drains
+constexpr unsigned long long kLandNs = 10000000ull;          // follower's wait for its copies after an abort
+
+enum OutKind { OUT_F64 = 0, OUT_I64 = 1, OUT_I64_RED = 2 };
 
 struct SmemCtl {
-    unsigned long long afull[NA], aempty[NA];
+    unsigned long long afull[NA], aempty[NA];  // afull / bfull: used in the leader only
     unsigned long long bfull[NB], bempty[NB];
-    unsigned long long tfull[2], tempty[2];
+    unsigned long long tfull[2], tempty[2];    // tempty: used in the leader only
     unsigned long long drain[ISSUERS];
     unsigned int tmem_base;
     volatile int abort;
-    long long rowoff[BM];
-    long long coloff[BN];   // -1 for columns beyond N
-    int eA[BM];
+    long long coloff[BN];                      // -1 for columns beyond N
     int eB[BN];
-    float stage[EPI_WARPS][32][17];
 };
 constexpr size_t SMEM_BYTES = 1024 + TILE_SMEM + sizeof(SmemCtl);
+static_assert(SMEM_BYTES <= 227 * 1024, "shared memory");
 
 struct Params {
     int M, N, K;
@@ -91,25 +105,42 @@ struct Params {
     int scale_base, beta, nslices;
     int ngroups;
     int glo[kMaxGroups], gn[kMaxGroups], gkc[kMaxGroups];
-    int epi, fixF;
-    int ksplit, kper;            // K split: CTA split s owns [s*kper, min(K, (s+1)*kper))
+    int out_kind, fixF;
+    int ksplit, kper;              // K split: item split s owns [s*kper, min(K, (s+1)*kper))
     long long tri_rdiv, tri_cdiv;  // triangular tile skip (0 = off)
-    int tiles_m, tiles_n, group_m;
+    int tiles_m, tiles_n, group_m, nitems;
     OutDesc out;
     int* status;
     unsigned long long wait_ns;
 };
 
-__device__ __forceinline__ uint32_t smem_u32(const void* p)
-{
-    return (uint32_t)__cvta_generic_to_shared(p);
-}
+__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
 __device__ __forceinline__ unsigned long long gtime()
 {
     unsigned long long t;
-    asm volatile("mov.u64 %0, %globaltimer;" : "=l"(t));
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
     return t;
+}
+
+__device__ __forceinline__ uint32_t cluster_rank()
+{
+    uint32_t r;
+    asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+    return r;
+}
+
+// Shared::cluster address of the object at the same offset in CTA `rank` of the cluster.
+__device__ __forceinline__ uint32_t peer_addr(uint32_t local, uint32_t rank)
+{
+    uint32_t r;
+    asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(local), "r"(rank));
+    return r;
+}
+
+__device__ __forceinline__ void cluster_sync()
+{
+    asm volatile("barrier.cluster.arrive.release.aligned;\nbarrier.cluster.wait.acquire.aligned;" ::: "memory");
 }
 
 __device__ __forceinline__ void mbar_init(unsigned long long* b, unsigned count)
@@ -129,37 +160,38 @@ __device__ __forceinline__ bool mbar_try(unsigned long long* b, uint32_t parity)
 }
 
 // Bounded wait; returns false (and raises the abort flag) when the bound expires
-// or another role has aborted.
-__device__ __noinline__ bool mbar_wait(unsigned long long* b, uint32_t parity, SmemCtl* ctl, int* status,
+// or another role has aborted.  Inlined: code under setmaxnreg calls no functions.
+__device__ __forceinline__ bool mbar_wait(unsigned long long* b, uint32_t parity, SmemCtl* ctl, int* status,
                                        unsigned long long limit_ns)
 {
     if (mbar_try(b, parity)) return true;
     const unsigned long long t0 = gtime();
     for (unsigned it = 1;; ++it) {
         if (mbar_try(b, parity)) return true;
-        if ((it & 63) == 0) {
+        // (each failed try_wait has already suspended the thread for a while)
+        if (it == 1 || (it & 7) == 0) {
             if (ctl->abort) return false;
             if (gtime() - t0 > limit_ns) {
                 ctl->abort = 1;
-                atomicOr(status, 1);
+                atomicOr(status, kStatusWaitExpired);
                 return false;
             }
         }
     }
 }
 
+__device__ __forceinline__ bool wait_fast(unsigned long long* b, uint32_t parity, SmemCtl* ctl, const Params& p)
+{
+    return mbar_try(b, parity) || mbar_wait(b, parity, ctl, p.status, p.wait_ns);
+}
+
 // Wait used only on the abort path: fixed bound, ignores the abort flag.
-__device__ __noinline__ void mbar_drain_wait(unsigned long long* b, uint32_t parity, int* status)
+__device__ __forceinline__ void mbar_drain_wait(unsigned long long* b, uint32_t parity, int* status)
 {
     const unsigned long long t0 = gtime();
     while (!mbar_try(b, parity)) {
-        if (gtime() - t0 > kDrainLimitNs) { atomicOr(status, 2); return; }
+        if (gtime() - t0 > kDrainLimitNs) { atomicOr(status, kStatusDrainExpired); return; }
     }
-}
-
-__device__ __forceinline__ void mbar_arrive(unsigned long long* b)
-{
-    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(b)) : "memory");
 }
 
 __device__ __forceinline__ void mbar_expect_tx(unsigned long long* b, uint32_t bytes)
@@ -167,11 +199,20 @@ __device__ __forceinline__ void mbar_expect_tx(unsigned long long* b, uint32_t b
     asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(b)), "r"(bytes) : "memory");
 }
 
-__device__ __forceinline__ void tma_load_3d(void* dst, const CUtensorMap* map, unsigned long long* bar, int x, int y, int z)
+// Arrive on the barrier at shared::cluster address `addr` (this CTA's or the peer's).
+__device__ __forceinline__ void mbar_arrive_cluster(uint32_t addr)
+{
+    asm volatile("mbarrier.arrive.release.cluster.shared::cluster.b64 _, [%0];" ::"r"(addr) : "memory");
+}
+
+// 2-CTA tile load: lands in this CTA's shared memory, completes on the barrier at
+// shared::cluster address `bar` (the leader's).
+__device__ __forceinline__ void tma_load_3d_pair(void* dst, const CUtensorMap* map, uint32_t bar, int x, int y, int z)
 {
     asm volatile(
-        "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], [%5];"
-        ::"r"(smem_u32(dst)), "l"((unsigned long long)map), "r"(x), "r"(y), "r"(z), "r"(smem_u32(bar))
+        "cp.async.bulk.tensor.3d.cta_group::2.shared::cluster.global.mbarrier::complete_tx::bytes"
+        " [%0], [%1, {%2, %3, %4}], [%5];"
+        ::"r"(smem_u32(dst)), "l"((unsigned long long)map), "r"(x), "r"(y), "r"(z), "r"(bar)
         : "memory");
 }
 
@@ -190,35 +231,35 @@ __device__ __forceinline__ unsigned long long smem_desc(const void* p)
 }
 
 // Instruction descriptor: FP32 accumulate, A/B format (1 = BF16, 2 = TF32),
-// both K-major, N = 256, M = 128.
+// both K-major, N = BN, M = 2 BM (the CTA pair).
 template <int KIND>
 __device__ __forceinline__ uint32_t instr_desc()
 {
     const uint32_t fmt = KIND == TC_BF16 ? 1u : 2u;
-    return (1u << 4) | (fmt << 7) | (fmt << 10) | ((uint32_t)(BN >> 3) << 17) | ((uint32_t)(BM >> 4) << 24);
+    return (1u << 4) | (fmt << 7) | (fmt << 10) | ((uint32_t)(BN >> 3) << 17) | ((uint32_t)((2 * BM) >> 4) << 24);
 }
 
 template <int KIND>
-__device__ __forceinline__ void mma(uint32_t tmem_d, unsigned long long adesc, unsigned long long bdesc, uint32_t idesc,
-                                    uint32_t accumulate)
+__device__ __forceinline__ void mma_pair(uint32_t tmem_d, unsigned long long adesc, unsigned long long bdesc,
+                                         uint32_t idesc, uint32_t accumulate)
 {
     if (KIND == TC_BF16) {
         asm volatile(
             "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
-            " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n"
+            " tcgen05.mma.cta_group::2.kind::f16 [%0], %1, %2, %3, p;\n}\n"
             ::"r"(tmem_d), "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate));
     } else {
         asm volatile(
             "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
-            " tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n"
+            " tcgen05.mma.cta_group::2.kind::tf32 [%0], %1, %2, %3, p;\n}\n"
             ::"r"(tmem_d), "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate));
     }
 }
 
-__device__ __forceinline__ void mma_commit(unsigned long long* bar)
+// Arrive on the barrier at shared::cluster address `bar` once this thread's prior MMAs complete.
+__device__ __forceinline__ void mma_commit(uint32_t bar)
 {
-    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
-                 : "memory");
+    asm volatile("tcgen05.commit.cta_group::2.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar) : "memory");
 }
 
 __device__ __forceinline__ void fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
@@ -234,14 +275,27 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&r)[16])
         : "r"(taddr));
 }
 
+// 32 lanes x 8 columns.
+__device__ __forceinline__ void tmem_ld8(uint32_t taddr, uint32_t (&r)[8])
+{
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7])
+                 : "r"(taddr));
+}
+
 __device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
 
-// Fire-and-forget int64 store / add for the fixed-point epilogue: no result, no ordering with
-// other memory operations, so the 16 of a sub-chunk issue back to back.
-__device__ __forceinline__ void st_cg_s64(long long* p, long long x)
+// Pins 8 running sums at this point of the instruction stream: their updates cannot sink
+// below the next (volatile) TMEM load, so one chunk's loaded values die before the next
+// chunk's arrive and the sums plus one chunk fit the epilogue's registers.
+template <typename T>
+__device__ __forceinline__ void pin8(T* x)
 {
-    asm volatile("st.global.cg.s64 [%0], %1;" ::"l"(p), "l"(x));
+    static_assert(sizeof(T) == 8, "8-byte sums");
+    long long* v = reinterpret_cast<long long*>(x);
+    asm volatile("" : "+l"(v[0]), "+l"(v[1]), "+l"(v[2]), "+l"(v[3]), "+l"(v[4]), "+l"(v[5]), "+l"(v[6]), "+l"(v[7]));
 }
+
 __device__ __forceinline__ void red_add_u64(long long* p, long long x)
 {
     asm volatile("red.relaxed.gpu.global.add.u64 [%0], %1;" ::"l"(p), "l"(x));
@@ -253,8 +307,38 @@ __device__ __forceinline__ double pow2(int e)
     return __longlong_as_double((long long)(e + 1023) << 52);
 }
 
-// Pass sequence shared by all roles: groups in order, each cut into K-chunks, over
-// this CTA's K range [kbeg, kend).
+// Epilogue-only named barrier (the 256 epilogue threads).
+__device__ __forceinline__ void epi_sync() { asm volatile("bar.sync 1, %0;" ::"n"(EPI_THREADS) : "memory"); }
+
+// Work item i: K split i / (tiles_m tiles_n), tile i % (tiles_m tiles_n), rastered in groups
+// of group_m tile rows so that the pairs resident at once share A and B tiles in L2.
+struct Item {
+    int split, m0, n0;
+    bool skip;
+};
+
+__device__ __forceinline__ Item item_of(const Params& p, int i)
+{
+    const int ntiles = p.tiles_m * p.tiles_n;
+    const int t = i % ntiles;
+    const int per_group = p.group_m * p.tiles_n;
+    const int first_m = (t / per_group) * p.group_m;
+    const int gm = min(p.tiles_m - first_m, p.group_m);
+    Item it;
+    it.split = i / ntiles;
+    it.m0 = (first_m + (t % per_group) % gm) * (2 * BM);
+    it.n0 = ((t % per_group) / gm) * BN;
+    // triangular skip: every element of the tile has b(n) < a(m)
+    it.skip = false;
+    if (p.tri_rdiv > 0) {
+        const long long nmax = min((long long)p.N - 1, (long long)it.n0 + BN - 1);
+        it.skip = nmax / p.tri_cdiv < (long long)it.m0 / p.tri_rdiv;
+    }
+    return it;
+}
+
+// Pass sequence of one item shared by all roles: groups in order, each cut into
+// K-chunks, over the item's K range [kbeg, kend).
 struct PassIter {
     int g, k0, k1, idx, kbeg, kend;
     __device__ int chunk_end(const Params& p, int from) const
@@ -287,7 +371,7 @@ struct PassIter {
     }
 };
 
-template <int KIND>
+template <int KIND, bool FIXED>
 __global__ void __launch_bounds__(THREADS, 1)
 gemm_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, const Params p)
 {
@@ -299,360 +383,307 @@ gemm_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
 
     constexpr int KSTEP = KIND == TC_BF16 ? 64 : 32;  // K elements per 128-byte row
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-
-    // grouped raster: consecutive CTAs walk group_m M-tiles before the next N-tile
-    const int per_group = p.group_m * p.tiles_n;
-    const int ntiles = p.tiles_m * p.tiles_n;            // tiles per K split
-    const int split = (int)blockIdx.x / ntiles;          // this CTA's K split
-    const int t = (int)blockIdx.x % ntiles;
-    const int first_m = (t / per_group) * p.group_m;
-    const int gm = min(p.tiles_m - first_m, p.group_m);
-    const int m0 = (first_m + (t % per_group) % gm) * BM;
-    const int n0 = ((t % per_group) / gm) * BN;
-    // triangular skip: every element of the tile has b(n) < a(m), so nothing of it is
-    // needed; leave before any barrier or TMEM is touched
-    if (p.tri_rdiv > 0) {
-        const long long nmax = min((long long)p.N - 1, (long long)n0 + BN - 1);
-        if (nmax / p.tri_cdiv < (long long)m0 / p.tri_rdiv) return;
-    }
+    const uint32_t rank = cluster_rank();
+    const bool leader = rank == 0;
+    const int pair = (int)(blockIdx.x >> 1), npairs = (int)(gridDim.x >> 1);
 
     if (threadIdx.x == 0) {
         for (int s = 0; s < NA; ++s) { mbar_init(&ctl->afull[s], 1); mbar_init(&ctl->aempty[s], ISSUERS); }
         for (int s = 0; s < NB; ++s) { mbar_init(&ctl->bfull[s], 1); mbar_init(&ctl->bempty[s], ISSUERS); }
-        for (int b = 0; b < 2; ++b) { mbar_init(&ctl->tfull[b], 1); mbar_init(&ctl->tempty[b], EPI_WARPS); }
+        for (int b = 0; b < 2; ++b) { mbar_init(&ctl->tfull[b], ISSUERS); mbar_init(&ctl->tempty[b], 2 * EPI_WARPS); }
         for (int q = 0; q < ISSUERS; ++q) mbar_init(&ctl->drain[q], 1);
         ctl->abort = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     if (warp == 1) {
-        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&ctl->tmem_base)),
+        asm volatile("tcgen05.alloc.cta_group::2.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&ctl->tmem_base)),
                      "r"(TMEM_COLS));
-        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
-    }
-    for (int r = threadIdx.x; r < BM; r += THREADS) {
-        const int m = m0 + r;
-        ctl->rowoff[r] = (m < p.M) ? map2(p.out.rmap, m) : -1;
-        ctl->eA[r] = (p.eA && m < p.M) ? p.eA[p.rowA0 + m] : 0;
-    }
-    for (int c = threadIdx.x; c < BN; c += THREADS) {
-        const int n = n0 + c;
-        ctl->eB[c] = (p.eB && n < p.N) ? p.eB[p.rowB0 + n] : 0;
-        ctl->coloff[c] = (n < p.N) ? map2(p.out.cmap, n) : -1;
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::2.sync.aligned;");
     }
     fence_before();
     __syncthreads();
+    cluster_sync();  // the peer's barriers are initialised before any copy or commit reaches them
     fence_after();
     const uint32_t tmem = ctl->tmem_base;
 
-    if (warp == 0) {
-        // ------------------------------------------------------------ producer
-        // Per K-step: for j = lo..hi, first the A tiles (in order i = hi..lo) down to
-        // the lowest i that B_j needs, then B_j.
-        if (lane == 0) {
+    if (warp < 4) {
+        asm volatile("setmaxnreg.dec.sync.aligned.u32 %0;" ::"n"(REG_LOW));
+        if (warp == 0 && lane == 0) {
+            // -------------------------------------------------------- producer
+            // Per K-step: for j = lo..hi, first the A tiles (in order i = hi..lo) down to
+            // the lowest i that B_j needs, then B_j.  Both CTAs load their halves into the
+            // same slots; the copies complete on the leader's full barriers, where the
+            // leader expects the bytes of both.
             asm volatile("prefetch.tensormap [%0];" ::"l"((unsigned long long)&tmA) : "memory");
             asm volatile("prefetch.tensormap [%0];" ::"l"((unsigned long long)&tmB) : "memory");
             long long a_issued = 0, b_issued = 0;
             bool ok = true;
-            PassIter it;
-            it.begin(p, split);
-            do {
-                int lo, hi;
-                it.ranges(p, lo, hi);
-                const int L1 = p.glo[it.g];
-                for (int kb = it.k0; kb < it.k1 && ok; kb += KSTEP) {
-                    int a_here = 0;
-                    for (int j = lo; j <= hi && ok; ++j) {
-                        const int imin = L1 - j > lo ? L1 - j : lo;
-                        while (a_here < hi - imin + 1) {
-                            const int as = (int)(a_issued & (NA - 1));
-                            const uint32_t par = (uint32_t)(((a_issued / NA) & 1) ^ 1);
-                            if (!mbar_try(&ctl->aempty[as], par) &&
-                                !mbar_wait(&ctl->aempty[as], par, ctl, p.status, p.wait_ns)) {
-                                ok = false;
-                                break;
+            for (int item = pair; item < p.nitems && ok; item += npairs) {
+                const Item w = item_of(p, item);
+                if (w.skip) continue;
+                PassIter it;
+                it.begin(p, w.split);
+                do {
+                    int lo, hi;
+                    it.ranges(p, lo, hi);
+                    const int L1 = p.glo[it.g];
+                    for (int kb = it.k0; kb < it.k1 && ok; kb += KSTEP) {
+                        int a_here = 0;
+                        for (int j = lo; j <= hi && ok; ++j) {
+                            const int imin = L1 - j > lo ? L1 - j : lo;
+                            while (a_here < hi - imin + 1) {
+                                const int as = (int)(a_issued % NA);
+                                const uint32_t par = (uint32_t)(((a_issued / NA) & 1) ^ 1);
+                                if (!wait_fast(&ctl->aempty[as], par, ctl, p)) { ok = false; break; }
+                                if (leader) mbar_expect_tx(&ctl->afull[as], 2 * A_TILE);
+                                tma_load_3d_pair(aring + as * A_TILE, &tmA, peer_addr(smem_u32(&ctl->afull[as]), 0),
+                                                 kb, (int)(p.rowA0 + w.m0 + (int)rank * BM), hi - a_here);
+                                ++a_issued;
+                                ++a_here;
                             }
-                            mbar_expect_tx(&ctl->afull[as], A_TILE);
-                            tma_load_3d(aring + as * A_TILE, &tmA, &ctl->afull[as], kb, (int)(p.rowA0 + m0), hi - a_here);
-                            ++a_issued;
-                            ++a_here;
+                            if (!ok) break;
+                            const int bs = (int)(b_issued % NB);
+                            const uint32_t bpar = (uint32_t)(((b_issued / NB) & 1) ^ 1);
+                            if (!wait_fast(&ctl->bempty[bs], bpar, ctl, p)) { ok = false; break; }
+                            if (leader) mbar_expect_tx(&ctl->bfull[bs], 2 * B_TILE);
+                            tma_load_3d_pair(bring + bs * B_TILE, &tmB, peer_addr(smem_u32(&ctl->bfull[bs]), 0), kb,
+                                             (int)(p.rowB0 + w.n0 + (int)rank * BNH), j);
+                            ++b_issued;
                         }
-                        if (!ok) break;
-                        const int bs = (int)(b_issued & (NB - 1));
-                        const uint32_t bpar = (uint32_t)(((b_issued / NB) & 1) ^ 1);
-                        if (!mbar_try(&ctl->bempty[bs], bpar) &&
-                            !mbar_wait(&ctl->bempty[bs], bpar, ctl, p.status, p.wait_ns)) {
-                            ok = false;
-                            break;
-                        }
-                        mbar_expect_tx(&ctl->bfull[bs], B_TILE);
-                        tma_load_3d(bring + bs * B_TILE, &tmB, &ctl->bfull[bs], kb, (int)(p.rowB0 + n0), j);
-                        ++b_issued;
                     }
-                }
-            } while (ok && it.next(p));
-            if (!ok) {
-                // drain: the newest copy into each A slot and each B slot may still be in flight
-                for (long long q = 1; q <= (a_issued < NA ? a_issued : NA); ++q) {
+                } while (ok && it.next(p));
+            }
+            if (ok) {
+                // tail: every slot's last use released, so no commit of the leader still
+                // targets this CTA's barriers when it leaves
+                for (long long q = 1; q <= (a_issued < NA ? a_issued : NA) && ok; ++q) {
                     const long long u = a_issued - q;
-                    mbar_drain_wait(&ctl->afull[u % NA], (uint32_t)((u / NA) & 1), p.status);
+                    ok = wait_fast(&ctl->aempty[u % NA], (uint32_t)((u / NA) & 1), ctl, p);
                 }
-                for (long long q = 1; q <= (b_issued < NB ? b_issued : NB); ++q) {
+                for (long long q = 1; q <= (b_issued < NB ? b_issued : NB) && ok; ++q) {
                     const long long u = b_issued - q;
-                    mbar_drain_wait(&ctl->bfull[u % NB], (uint32_t)((u / NB) & 1), p.status);
+                    ok = wait_fast(&ctl->bempty[u % NB], (uint32_t)((u / NB) & 1), ctl, p);
                 }
             }
-        }
-    } else if (warp <= ISSUERS) {
-        // ----------------------------------------------------------------- MMA
-        // Two issuing warps: issuing one tcgen05.mma costs the issuing thread about half
-        // of the MMA's own duration and the hardware queue is shallow, so a single issuer
-        // with per-tile barrier bookkeeping leaves the tensor pipe idle.  In a two-level
-        // pass issuer `me` owns level L1+me and its accumulator; both walk the same tile
-        // sequence, wait for the same tiles and release every slot (arrival count 2), so
-        // neither can run a phase ahead of the other.  In a one-level pass issuer 0 does
-        // all MMAs and issuer 1 only paces and releases.  Bookkeeping stays in registers;
-        // slot descriptors are slot 0's plus an offset; barrier tests take an inline fast path.
-        if (lane == 0) {
+            if (!ok) {
+                if (leader) {
+                    // the newest copy into each slot may still be in flight
+                    for (long long q = 1; q <= (a_issued < NA ? a_issued : NA); ++q) {
+                        const long long u = a_issued - q;
+                        mbar_drain_wait(&ctl->afull[u % NA], (uint32_t)((u / NA) & 1), p.status);
+                    }
+                    for (long long q = 1; q <= (b_issued < NB ? b_issued : NB); ++q) {
+                        const long long u = b_issued - q;
+                        mbar_drain_wait(&ctl->bfull[u % NB], (uint32_t)((u / NB) & 1), p.status);
+                    }
+                } else {
+                    // the follower's copies complete on the leader's barriers: give them time to land
+                    const unsigned long long t0 = gtime();
+                    while (gtime() - t0 < kLandNs) {}
+                }
+            }
+        } else if (leader && (warp == 1 || warp == 2) && lane == 0) {
+            // ------------------------------------------------------------ MMA
+            // Issuer `me` owns level L1 + me of a two-level pass (columns me * BN of the
+            // pass's buffer); in a one-level pass issuer 0 does all MMAs and issuer 1 only
+            // paces, releases and commits.  Both walk the same tile sequence, wait for the
+            // same tiles and release every slot in both CTAs (arrival count 2 each).
             const int me = warp - 1;
             const uint32_t idesc = instr_desc<KIND>();
             // slot q's descriptor = slot 0's + q * tile_bytes / 16 in the start-address field
             // (shared addresses stay below 256 KB, so the 14-bit field never carries over)
             const unsigned long long adesc0 = smem_desc(aring), bdesc0 = smem_desc(bring);
-            uint32_t a_used = 0, b_used = 0;
-            uint32_t tuse0 = 0, tuse1 = 0;
-            int toggle = 0;
+            const uint32_t aempty0 = smem_u32(&ctl->aempty[0]), bempty0 = smem_u32(&ctl->bempty[0]);
+            const uint32_t aempty1 = peer_addr(aempty0, 1), bempty1 = peer_addr(bempty0, 1);
+            const uint32_t tfull0 = smem_u32(&ctl->tfull[0]), tfull1 = peer_addr(tfull0, 1);
+            uint32_t a_used = 0, b_used = 0, npass = 0;
             bool ok = true, any = false;
-            PassIter it;
-            it.begin(p, split);
-            do {
-                int lo, hi;
-                it.ranges(p, lo, hi);
-                const int L1 = p.glo[it.g], nl = p.gn[it.g], L2 = L1 + nl - 1;
-                const bool active = me < nl;
-                const int buf = nl == 2 ? me : toggle;
-                if (nl == 1) toggle ^= 1;
-                const int mylevel = L1 + me;
-                if (active) {
-                    const uint32_t par = ((buf ? tuse1 : tuse0) & 1) ^ 1;
-                    if (!mbar_try(&ctl->tempty[buf], par) && !mbar_wait(&ctl->tempty[buf], par, ctl, p.status, p.wait_ns))
-                        ok = false;
-                }
-                if (!ok) break;
-                fence_after();
-                const uint32_t d = tmem + (uint32_t)(buf * BN);
-                uint32_t acc = 0;
-                for (int kb = it.k0; kb < it.k1 && ok; kb += KSTEP) {
-                    int a_wait = 0, a_free = 0;  // A tiles of this K-step waited for / released (i = hi - index)
-                    for (int j = lo; j <= hi; ++j) {
-                        const int imin = L1 - j > lo ? L1 - j : lo;
-                        while (a_wait < hi - imin + 1) {
-                            const uint32_t u = a_used + (uint32_t)a_wait;
-                            unsigned long long* bar = &ctl->afull[u & (NA - 1)];
-                            const uint32_t par = (u / NA) & 1;
-                            if (!mbar_try(bar, par) && !mbar_wait(bar, par, ctl, p.status, p.wait_ns)) {
-                                ok = false;
-                                break;
+            for (int item = pair; item < p.nitems && ok; item += npairs) {
+                const Item w = item_of(p, item);
+                if (w.skip) continue;
+                PassIter it;
+                it.begin(p, w.split);
+                do {
+                    int lo, hi;
+                    it.ranges(p, lo, hi);
+                    const int L1 = p.glo[it.g], nl = p.gn[it.g];
+                    const bool active = me < nl;
+                    const int mylevel = L1 + me;
+                    const int buf = (int)(npass & 1);
+                    const uint32_t use = npass >> 1;  // earlier passes on this buffer
+                    if (!wait_fast(&ctl->tempty[buf], (use & 1) ^ 1, ctl, p)) { ok = false; break; }
+                    fence_after();
+                    const uint32_t d = tmem + (uint32_t)(buf * 2 * BN + me * BN);
+                    uint32_t acc = 0;
+                    for (int kb = it.k0; kb < it.k1 && ok; kb += KSTEP) {
+                        int a_wait = 0, a_free = 0;  // A tiles of this K-step waited for / released
+                        for (int j = lo; j <= hi; ++j) {
+                            const int imin = L1 - j > lo ? L1 - j : lo;
+                            while (a_wait < hi - imin + 1) {
+                                const uint32_t u = a_used + (uint32_t)a_wait;
+                                if (!wait_fast(&ctl->afull[u % NA], (u / NA) & 1, ctl, p)) { ok = false; break; }
+                                ++a_wait;
                             }
-                            ++a_wait;
-                        }
-                        if (!ok) break;
-                        const int bs = (int)(b_used & (NB - 1));
-                        {
-                            unsigned long long* bar = &ctl->bfull[bs];
-                            const uint32_t par = (b_used / NB) & 1;
-                            if (!mbar_try(bar, par) && !mbar_wait(bar, par, ctl, p.status, p.wait_ns)) {
-                                ok = false;
-                                break;
-                            }
-                        }
-                        if (active) {
-                            const unsigned long long bd = bdesc0 + ((unsigned long long)bs << 11);
-                            // products of my level(s) with this B slice
-                            const int i_hi = (nl == 2 ? mylevel : L2) - j < hi ? (nl == 2 ? mylevel : L2) - j : hi;
-                            const int i_lo = (nl == 2 ? mylevel : L1) - j > lo ? (nl == 2 ? mylevel : L1) - j : lo;
-                            for (int i = i_hi; i >= i_lo; --i) {
+                            if (!ok) break;
+                            const uint32_t bs = b_used % NB;
+                            if (!wait_fast(&ctl->bfull[bs], (b_used / NB) & 1, ctl, p)) { ok = false; break; }
+                            fence_after();
+                            const int i = mylevel - j;
+                            if (active && i >= lo && i <= hi) {
+                                const unsigned long long bd = bdesc0 + ((unsigned long long)bs * (B_TILE >> 4));
                                 const unsigned long long ad =
-                                    adesc0 + ((unsigned long long)((a_used + (uint32_t)(hi - i)) & (NA - 1)) << 10);
+                                    adesc0 + ((unsigned long long)((a_used + (uint32_t)(hi - i)) % NA) * (A_TILE >> 4));
                                 // four MMAs per 128-byte row: advance the start address by 32 bytes each
-                                mma<KIND>(d, ad, bd, idesc, acc);
-                                mma<KIND>(d, ad + 2, bd + 2, idesc, 1u);
-                                mma<KIND>(d, ad + 4, bd + 4, idesc, 1u);
-                                mma<KIND>(d, ad + 6, bd + 6, idesc, 1u);
+                                mma_pair<KIND>(d, ad, bd, idesc, acc);
+                                mma_pair<KIND>(d, ad + 2, bd + 2, idesc, 1u);
+                                mma_pair<KIND>(d, ad + 4, bd + 4, idesc, 1u);
+                                mma_pair<KIND>(d, ad + 6, bd + 6, idesc, 1u);
                                 acc = 1;
                                 any = true;
                             }
+                            mma_commit(bempty0 + bs * 8);
+                            mma_commit(bempty1 + bs * 8);
+                            ++b_used;
+                            // release the A tiles no later B of this K-step needs: i > min(hi, L2 - j - 1)
+                            const int L2 = L1 + nl - 1;
+                            const int keep = j < hi ? (L2 - j - 1 < hi ? L2 - j - 1 : hi) : lo - 1;
+                            while (a_free < hi - keep) {
+                                const uint32_t as = (a_used + (uint32_t)a_free) % NA;
+                                mma_commit(aempty0 + as * 8);
+                                mma_commit(aempty1 + as * 8);
+                                ++a_free;
+                            }
                         }
-                        mma_commit(&ctl->bempty[bs]);
-                        ++b_used;
-                        // release the A tiles no later B of this K-step needs: i > min(hi, L2 - j - 1)
-                        const int keep = j < hi ? (L2 - j - 1 < hi ? L2 - j - 1 : hi) : lo - 1;
-                        while (a_free < hi - keep) {
-                            mma_commit(&ctl->aempty[(a_used + (uint32_t)a_free) & (NA - 1)]);
-                            ++a_free;
-                        }
+                        if (!ok) break;
+                        a_used += (uint32_t)(hi - lo + 1);
                     }
                     if (!ok) break;
-                    a_used += (uint32_t)(hi - lo + 1);
-                }
-                if (!ok) break;
-                if (active) {
-                    mma_commit(&ctl->tfull[buf]);
-                    if (buf) ++tuse1; else ++tuse0;
-                }
-            } while (it.next(p));
-            if (!ok && any) {
-                mma_commit(&ctl->drain[me]);
+                    mma_commit(tfull0 + buf * 8);
+                    mma_commit(tfull1 + buf * 8);
+                    ++npass;
+                } while (it.next(p));
+            }
+            if (ok && me == 0) {
+                // tail: both buffers' last drains (the follower's arrivals land here) are done
+                for (uint32_t q = npass > 2 ? npass - 2 : 0; q < npass && ok; ++q)
+                    ok = wait_fast(&ctl->tempty[q & 1], (q >> 1) & 1, ctl, p);
+            }
+            if (any) {
+                // every MMA this thread issued has completed before TMEM is released
+                mma_commit(smem_u32(&ctl->drain[me]));
                 mbar_drain_wait(&ctl->drain[me], 0, p.status);
             }
         }
     } else {
+        asm volatile("setmaxnreg.inc.sync.aligned.u32 %0;" ::"n"(REG_HIGH));
         // ------------------------------------------------------------ epilogue
-        // Warp e = warp - 1 - ISSUERS may read TMEM lanes 32 (warp % 4) .. + 31 (rows row0..) and
-        // owns columns half*128 .. +127 of the tile, in sub-chunks of 16 columns.  A sub-chunk
-        // of one level is read lane = row, staged, and re-read lane = column: lane L handles
-        // column cl = L % 16 of rows 2k + rp (rp = L / 16, k < 16).
-        const int e = warp - 1 - ISSUERS;
+        // Warp e = warp - 4 reads TMEM lanes 32 (warp % 4) .. + 31 and owns columns
+        // half * 64 .. + 63 of the tile: one output row and 64 columns per thread.
+        const int e = warp - 4;
         const int q4 = warp & 3;
-        const int row0 = q4 * 32;
+        const int row = q4 * 32 + lane;  // TMEM lane = row of this CTA's 128
         const int half = e >> 2;
-        const int cl = lane & 15, rp = lane >> 4;
-        float(*stg)[17] = ctl->stage[e];
-        // output row offsets of this lane's 16 rows (fixed for the CTA), kept in registers
-        long long ro_reg[16];
-#pragma unroll
-        for (int k = 0; k < 16; ++k) ro_reg[k] = ctl->rowoff[row0 + 2 * k + rp];
-        uint32_t tuse0 = 0, tuse1 = 0;
-        int toggle = 0;
-        PassIter it;
-        it.begin(p, split);
+        const uint32_t tl = tmem + ((uint32_t)(q4 * 32) << 16);
+        const uint32_t tempty0 = peer_addr(smem_u32(&ctl->tempty[0]), 0);
+        typedef typename std::conditional<FIXED, long long, double>::type acc_t;
+        acc_t sum[COLS_PER_THREAD];
+        uint32_t npass = 0;
         bool ok = true;
-        // one level of one sub-chunk, from registers r (lane = row) to a[k] = acc(row0 + 2k + rp, col + cl)
-        auto transpose = [&](const uint32_t (&r)[16], float (&a)[16]) {
+        // Every epilogue warp walks all items and meets every epi_sync even after an abort
+        // (it then skips the waits and TMEM reads), so no warp can be left at a named
+        // barrier that a warp which gave up will never reach.
+        for (int item = pair; item < p.nitems; item += npairs) {
+            const Item w = item_of(p, item);
+            if (w.skip) continue;
+            // this item's output row and column tables (the previous item's writes are done)
+            const int m = w.m0 + (int)rank * BM + row;
+            const long long ro = (m < p.M) ? map2(p.out.rmap, m) : -1;
+            const int eAr = (p.eA && m < p.M) ? p.eA[p.rowA0 + m] : 0;
+            epi_sync();
+            for (int c = e * 32 + lane; c < BN; c += EPI_THREADS) {
+                const int n = w.n0 + c;
+                ctl->coloff[c] = (n < p.N) ? map2(p.out.cmap, n) : -1;
+                ctl->eB[c] = (p.eB && n < p.N) ? p.eB[p.rowB0 + n] : 0;
+            }
+            epi_sync();
+            PassIter it;
+            it.begin(p, w.split);
+            do {
+                const int L1 = p.glo[it.g], nl = p.gn[it.g];
+                const int buf = (int)(npass & 1);
+                if (ok && !wait_fast(&ctl->tfull[buf], (npass >> 1) & 1, ctl, p)) ok = false;
+                if (!ok) continue;  // (continue in a do-while goes to it.next())
+                fence_after();
+                const bool first = it.idx == 0;
+                const int sh = p.fixF - p.beta * (L1 + nl - 1);
+                const uint32_t tb = tl + (uint32_t)(buf * 2 * BN + half * COLS_PER_THREAD);
 #pragma unroll
-            for (int j = 0; j < 16; ++j) stg[lane][j] = __uint_as_float(r[j]);
-            __syncwarp();
+                for (int cc = 0; cc < COLS_PER_THREAD / 8; ++cc) {
+                    uint32_t r0[8], r1[8];
+                    tmem_ld8(tb + (uint32_t)(cc * 8), r0);
+                    if (nl == 2) tmem_ld8(tb + (uint32_t)(BN + cc * 8), r1);
+                    tmem_wait_ld();
+                    if (cc == COLS_PER_THREAD / 8 - 1) {
+                        // the buffer is read: hand it back to the MMA issuers
+                        fence_before();
+                        __syncwarp();
+                        if (lane == 0) mbar_arrive_cluster(tempty0 + buf * 8);
+                    }
+                    if (FIXED) {
+                        // exact int64 fixed point (2^-fixF of a level-0 unit); a level pair is combined
+                        // as (acc_L1 * 2^beta + acc_L2) before the one shift to the fixed-point scale
 #pragma unroll
-            for (int k = 0; k < 16; ++k) a[k] = stg[2 * k + rp][cl];
-            __syncwarp();
-        };
-        do {
-            const int L1 = p.glo[it.g], nl = p.gn[it.g];
-            // buffer of level L1 + q is (q ? 1 : buf0)
-            const int buf0 = nl == 2 ? 0 : toggle;
-            const int nb = nl;
-            const bool use0 = nl == 2 || buf0 == 0, use1 = nl == 2 || buf0 == 1;
-            if (nl == 1) toggle ^= 1;
-            if (use0 && !mbar_wait(&ctl->tfull[0], tuse0 & 1, ctl, p.status, p.wait_ns)) ok = false;
-            if (ok && use1 && !mbar_wait(&ctl->tfull[1], tuse1 & 1, ctl, p.status, p.wait_ns)) ok = false;
-            if (!ok) break;
-            fence_after();
-            const bool first = it.idx == 0, last = it.last(p);
-            const uint32_t tl = tmem + ((uint32_t)row0 << 16);
-            for (int sc = 0; sc < BN / 32; ++sc) {
-                const int col = half * (BN / 2) + sc * 16;  // tile column of the sub-chunk
-                const long long co = ctl->coloff[col + cl];
-                const bool ncol = co >= 0;
-                float a0[16], a1[16];
-                uint32_t r0[16], r1[16];
-                tmem_ld16(tl + (uint32_t)(buf0 * BN + col), r0);
-                if (nb == 2) tmem_ld16(tl + (uint32_t)(BN + col), r1);
-                tmem_wait_ld();
-                transpose(r0, a0);
-                if (nb == 2) transpose(r1, a1);
-                if (p.epi != EPI_FP64_RMW) {
-                    // exact int64 fixed point (2^-fixF of a level-0 unit); a level pair is combined
-                    // as (acc_L1 * 2^beta + acc_L2) before the one shift to the fixed-point scale
-                    long long X[16];
-                    const int sh = p.fixF - p.beta * (L1 + nb - 1);
-                    if (nb == 2) {
-#pragma unroll
-                        for (int k = 0; k < 16; ++k)
-                            X[k] = ((long long)__float2int_rn(a0[k]) << p.beta) + (long long)__float2int_rn(a1[k]);
+                        for (int k = 0; k < 8; ++k) {
+                            long long X = (long long)__float2int_rn(__uint_as_float(r0[k]));
+                            if (nl == 2) X = (X << p.beta) + (long long)__float2int_rn(__uint_as_float(r1[k]));
+                            X = sh >= 0 ? (X << sh) : ((X + (1ll << (-sh - 1))) >> (-sh));
+                            sum[cc * 8 + k] = first ? (acc_t)X : sum[cc * 8 + k] + (acc_t)X;
+                        }
                     } else {
 #pragma unroll
-                        for (int k = 0; k < 16; ++k) X[k] = (long long)__float2int_rn(a0[k]);
+                        for (int k = 0; k < 8; ++k) {
+                            const double X = (double)__uint_as_float(r0[k]);
+                            sum[cc * 8 + k] = first ? (acc_t)X : sum[cc * 8 + k] + (acc_t)X;
+                        }
                     }
-                    if (sh >= 0) {
+                    pin8(&sum[cc * 8]);
+                }
+                ++npass;
+                if (it.last(p) && ro >= 0) {
+                    // the item's result: one row, 64 columns of this thread
+                    const int col0 = half * COLS_PER_THREAD;
+                    double* Crow = p.out.C + ro;
+                    const int ebase = eAr + p.scale_base - (FIXED ? p.fixF : 0);
 #pragma unroll
-                        for (int k = 0; k < 16; ++k) X[k] <<= sh;
-                    } else {
-                        const long long rnd = 1ll << (-sh - 1);
+                    for (int k0 = 0; k0 < COLS_PER_THREAD; k0 += 8) {
+                        // eight columns at a time: keeps the table loads from being hoisted
+                        // ahead of all stores (they would need more registers than the sums leave)
+                        asm volatile("" ::: "memory");
 #pragma unroll
-                        for (int k = 0; k < 16; ++k) X[k] = (X[k] + rnd) >> (-sh);
-                    }
-                    if (p.epi == EPI_FIXED64_RED || p.epi == EPI_FIXED64_ADD) {
-                        // int64 result for a consumer that scales it: store (first pass of an
-                        // unsplit tile), then add without reading
-                        const bool store = first && p.epi == EPI_FIXED64_RED;
-                        if (ncol) {
-                            long long* cb = (long long*)(p.out.C + co);
-                            if (store) {
-#pragma unroll
-                                for (int k = 0; k < 16; ++k)
-                                    if (ro_reg[k] >= 0) st_cg_s64(cb + ro_reg[k], X[k]);
+                        for (int k = k0; k < k0 + 8; ++k) {
+                            const long long co = ctl->coloff[col0 + k];
+                            if (co < 0) continue;
+                            if (p.out_kind == OUT_F64) {
+                                const double val = (double)sum[k] * pow2(ebase + ctl->eB[col0 + k]);
+                                Crow[co] = p.out.accumulate ? Crow[co] + val : val;
+                            } else if (p.out_kind == OUT_I64) {
+                                __stcg((long long*)(Crow + co), (long long)sum[k]);
                             } else {
-#pragma unroll
-                                for (int k = 0; k < 16; ++k)
-                                    if (ro_reg[k] >= 0) red_add_u64(cb + ro_reg[k], X[k]);
+                                red_add_u64((long long*)(Crow + co), (long long)sum[k]);
                             }
                         }
-                        continue;
-                    }
-                    // all loads of the sub-chunk are issued before any store (no aliasing stalls)
-                    if (!first) {
-#pragma unroll
-                        for (int k = 0; k < 16; ++k) {
-                            const long long ro = ctl->rowoff[row0 + 2 * k + rp];
-                            if (ro >= 0 && ncol) X[k] += __ldcg((const long long*)(p.out.C + ro + co));
-                        }
-                    }
-                    const int eb = ctl->eB[col + cl] + p.scale_base - p.fixF;
-#pragma unroll
-                    for (int k = 0; k < 16; ++k) {
-                        const int r = row0 + 2 * k + rp;
-                        const long long ro = ctl->rowoff[r];
-                        if (ro < 0 || !ncol) continue;
-                        long long* dst = (long long*)(p.out.C + ro + co);
-                        if (last) __stcg((double*)dst, (double)X[k] * pow2(ctl->eA[r] + eb));
-                        else __stcg(dst, X[k]);
-                    }
-                } else {
-                    // FP64 read-modify-write of 2^e * acc (both levels of a pair at once)
-                    const bool store_only = first && !p.out.accumulate;
-                    const int eb0 = ctl->eB[col + cl] + p.scale_base - p.beta * L1;
-                    double old[16];
-#pragma unroll
-                    for (int k = 0; k < 16; ++k) {
-                        const long long ro = ctl->rowoff[row0 + 2 * k + rp];
-                        old[k] = (!store_only && ro >= 0 && ncol) ? __ldcg(p.out.C + ro + co) : 0.0;
-                    }
-#pragma unroll
-                    for (int k = 0; k < 16; ++k) {
-                        const int r = row0 + 2 * k + rp;
-                        const long long ro = ctl->rowoff[r];
-                        if (ro < 0 || !ncol) continue;
-                        double val = (double)a0[k] * pow2(ctl->eA[r] + eb0);
-                        if (nb == 2) val += (double)a1[k] * pow2(ctl->eA[r] + eb0 - p.beta);
-                        __stcg(p.out.C + ro + co, old[k] + val);
                     }
                 }
-            }
-            fence_before();
-            __syncwarp();
-            if (lane == 0) {
-                if (use0) mbar_arrive(&ctl->tempty[0]);
-                if (use1) mbar_arrive(&ctl->tempty[1]);
-            }
-            if (use0) ++tuse0;
-            if (use1) ++tuse1;
-        } while (it.next(p));
+            } while (it.next(p));
+        }
     }
 
     fence_before();
     __syncthreads();
+    cluster_sync();  // no CTA leaves while its peer may still read its shared memory or signal it
     fence_after();
     if (warp == 1) {
-        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TMEM_COLS));
+        asm volatile("tcgen05.dealloc.cta_group::2.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TMEM_COLS));
     }
 }
 
@@ -686,6 +717,42 @@ bool make_map(CUtensorMap* m, const void* base, int kind, long long K, long long
                      const_cast<void*>(base), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
                      CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     return r == CUDA_SUCCESS;
+}
+
+template <int KIND, bool FIXED>
+cudaError_t launch(const CUtensorMap& ma, const CUtensorMap& mb, const Params& p, cudaStream_t s)
+{
+    static std::once_flag once;
+    static cudaError_t attr_err = cudaSuccess;
+    static int max_pairs = 0;
+    cudaLaunchConfig_t cfg{};
+    cfg.blockDim = dim3(THREADS);
+    cfg.dynamicSmemBytes = SMEM_BYTES;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = 2;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    std::call_once(once, [&cfg] {
+        attr_err = cudaFuncSetAttribute(gemm_tc_kernel<KIND, FIXED>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                        (int)SMEM_BYTES);
+        // persistent: as many pairs as are resident on the device at once
+        int n = 0;
+        cfg.gridDim = dim3(2 * 64);
+        if (attr_err != cudaSuccess ||
+            cudaOccupancyMaxActiveClusters(&n, gemm_tc_kernel<KIND, FIXED>, &cfg) != cudaSuccess || n <= 0) {
+            cudaGetLastError();
+            n = device_sm_count() / 2;
+        }
+        max_pairs = n;
+    });
+    if (attr_err != cudaSuccess) return attr_err;
+    const int pairs = p.nitems < max_pairs ? p.nitems : max_pairs;
+    cfg.gridDim = dim3((unsigned)(2 * pairs));
+    return cudaLaunchKernelEx(&cfg, gemm_tc_kernel<KIND, FIXED>, ma, mb, p);
 }
 
 }  // namespace
@@ -745,6 +812,7 @@ cudaError_t gemm_tc(const GemmTc& g, cudaStream_t s)
     if (g.K <= 0 || g.slices < 1 || g.slices > MAX_SLICES || g.ngroups < 1 || g.ngroups > kMaxGroups)
         return cudaErrorInvalidValue;
     const int kstep = g.kind == TC_BF16 ? 64 : 32;
+    const bool fixed = g.epi != EPI_FP64_RMW;
     Params p{};
     p.M = g.M; p.N = g.N; p.K = g.K;
     p.rowA0 = g.rowA0; p.rowB0 = g.rowB0;
@@ -755,40 +823,35 @@ cudaError_t gemm_tc(const GemmTc& g, cudaStream_t s)
         if (g.gn[i] < 1 || g.gn[i] > 2 || g.glo[i] < 0 || g.glo[i] + g.gn[i] - 1 > 2 * (g.slices - 1))
             return cudaErrorInvalidValue;
         if (g.gkc[i] < 0 || g.gkc[i] % kstep) return cudaErrorInvalidValue;
+        if (!fixed && g.gn[i] != 1) return cudaErrorInvalidValue;  // FP64 sums take one level per pass
         p.glo[i] = g.glo[i]; p.gn[i] = g.gn[i]; p.gkc[i] = g.gkc[i];
     }
-    if (g.epi != EPI_FP64_RMW && g.out.accumulate) return cudaErrorInvalidValue;
-    p.epi = g.epi;
+    if ((g.epi == EPI_FIXED64_RED || g.epi == EPI_FIXED64_ADD) && g.out.accumulate) return cudaErrorInvalidValue;
+    p.out_kind = g.epi == EPI_FIXED64_RED ? OUT_I64 : (g.epi == EPI_FIXED64_ADD ? OUT_I64_RED : OUT_F64);
     p.fixF = g.fixF;
     p.ksplit = g.ksplit > 1 ? g.ksplit : 1;
     if (p.ksplit > 1 && g.epi != EPI_FIXED64_ADD) return cudaErrorInvalidValue;
     p.kper = (int)((((long long)g.K + p.ksplit - 1) / p.ksplit + kstep - 1) / kstep * kstep);
-    for (int i = 0; i < g.ngroups; ++i)
-        if (p.ksplit > 1 && g.gkc[i] != 0) return cudaErrorInvalidValue;
     if ((g.tri_rdiv > 0) != (g.tri_cdiv > 0) || g.tri_rdiv < 0) return cudaErrorInvalidValue;
     p.tri_rdiv = g.tri_rdiv;
     p.tri_cdiv = g.tri_cdiv;
     p.out = g.out;
     p.status = g.status;
     p.wait_ns = g.wait_ns;
-    p.tiles_m = (g.M + BM - 1) / BM;
+    p.tiles_m = (g.M + 2 * BM - 1) / (2 * BM);
     p.tiles_n = (g.N + BN - 1) / BN;
     p.group_m = p.tiles_m < 8 ? p.tiles_m : 8;
+    const long long nitems = (long long)p.tiles_m * p.tiles_n * p.ksplit;
+    if (nitems > 0x7fffffffll) return cudaErrorInvalidConfiguration;
+    p.nitems = (int)nitems;
     CUtensorMap ma, mb;
     if (!make_map(&ma, g.A, g.kind, g.K, g.pitchA, g.rowsA, g.slices, BM)) return cudaErrorInvalidValue;
-    if (!make_map(&mb, g.B, g.kind, g.K, g.pitchB, g.rowsB, g.slices, BN)) return cudaErrorInvalidValue;
-    const long long nctas = (long long)p.tiles_m * p.tiles_n * p.ksplit;
-    if (nctas > 0x7fffffffll) return cudaErrorInvalidConfiguration;
-    static std::once_flag once;
-    std::call_once(once, [] {
-        cudaFuncSetAttribute(gemm_tc_kernel<TC_BF16>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SMEM_BYTES);
-        cudaFuncSetAttribute(gemm_tc_kernel<TC_TF32>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SMEM_BYTES);
-    });
+    if (!make_map(&mb, g.B, g.kind, g.K, g.pitchB, g.rowsB, g.slices, BNH)) return cudaErrorInvalidValue;
     cudaError_t err;
     if (g.kind == TC_BF16)
-        err = (gemm_tc_kernel<TC_BF16><<<(unsigned)nctas, THREADS, SMEM_BYTES, s>>>(ma, mb, p), cudaGetLastError());
+        err = fixed ? launch<TC_BF16, true>(ma, mb, p, s) : launch<TC_BF16, false>(ma, mb, p, s);
     else
-        err = (gemm_tc_kernel<TC_TF32><<<(unsigned)nctas, THREADS, SMEM_BYTES, s>>>(ma, mb, p), cudaGetLastError());
+        err = fixed ? launch<TC_TF32, true>(ma, mb, p, s) : launch<TC_TF32, false>(ma, mb, p, s);
     if (err != cudaSuccess) return err;
     count_launch();
     return cudaGetLastError();

@@ -309,18 +309,26 @@ cudaError_t split_rows_bf16(const RowSrc& src, int s, int beta, void* D, long lo
     return cudaGetLastError();
 }
 
+cudaError_t cols_max(const ColSrc& src, unsigned long long* mx, int* status, cudaStream_t st)
+{
+    if (src.rows <= 0 || src.K <= 0) return cudaSuccess;
+    const long long kchunk = 256;
+    dim3 g((unsigned)((src.rows + 255) / 256), (unsigned)std::min(65535ll, (src.K + kchunk - 1) / kchunk));
+    col_max_kernel<<<g, 256, 0, st>>>(src, kchunk, mx, status);
+    count_launch();
+    return cudaGetLastError();
+}
+
 cudaError_t split_cols_bf16(const ColSrc& src, int s, int beta, void* D, long long pitch, int* e,
-                            unsigned long long* scratch_max, int* status, cudaStream_t st)
+                            unsigned long long* scratch_max, int* status, cudaStream_t st, bool premax)
 {
     if (src.rows <= 0) return cudaSuccess;
     if (s < 0 || s > 8 || (s > 0 && (beta < 2 || beta > 9 || beta * s > 62))) return cudaErrorInvalidValue;
-    if (s > 0) {
+    if (s > 0 && !premax) {
         cudaError_t err = cudaMemsetAsync(scratch_max, 0, sizeof(unsigned long long) * src.rows, st);
         if (err != cudaSuccess) return err;
-        const long long kchunk = 256;
-        dim3 g((unsigned)((src.rows + 255) / 256), (unsigned)std::min(65535ll, (src.K + kchunk - 1) / kchunk));
-        col_max_kernel<<<g, 256, 0, st>>>(src, kchunk, scratch_max, status);
-        count_launch();
+        err = cols_max(src, scratch_max, status, st);
+        if (err != cudaSuccess) return err;
     }
     dim3 g2((unsigned)((src.rows + CT_R - 1) / CT_R), (unsigned)std::min(65535ll, (src.K + CT_K - 1) / CT_K));
     split_cols_kernel<<<g2, dim3(32, 8), 0, st>>>(src, s, beta, scratch_max, (__nv_bfloat16*)D, pitch, e);

@@ -311,8 +311,9 @@ def test_a_range_shards_assemble(dev, oracle, mode):
     Lg, tg = cu(L, dev), cu(t2, dev)
     R_ref = oracle.ladder(L, t2)
     for sym in (False, True):
-        full = B.ladder_forward(Lg, tg, mode=mode, symmetric=sym)
-        bounds = B.partition(o, v, n, 3, mode=mode, symmetric=sym)
+        # integral-first: the pair-symmetric path whose ranges own their energy terms
+        full = B.ladder_forward(Lg, tg, mode=mode, symmetric=sym, order="integral_first")
+        bounds = B.partition(o, v, n, 3, mode=mode, symmetric=sym, order="integral_first")
         assert bounds[0] == 0 and bounds[-1] == v
         parts = torch.zeros_like(full)
         e_sum = 0.0
@@ -320,12 +321,13 @@ def test_a_range_shards_assemble(dev, oracle, mode):
             lo, hi = bounds[g], bounds[g + 1]
             Rp = torch.zeros_like(full)
             if sym:
-                _, Eg = B.ladder_forward(Lg, tg, R=Rp, mode=mode, symmetric=sym, a_range=(lo, hi), energy=True)
+                _, Eg = B.ladder_forward(Lg, tg, R=Rp, mode=mode, symmetric=sym, a_range=(lo, hi), energy=True,
+                                         order="integral_first")
                 e_g = float(Eg)
                 assert abs(e_g - oracle.energy_range(R_ref, t2, lo, hi)) <= TOL[mode] * abs(oracle.energy(R_ref, t2))
                 e_sum += e_g
             else:
-                B.ladder_forward(Lg, tg, R=Rp, mode=mode, symmetric=sym, a_range=(lo, hi))
+                B.ladder_forward(Lg, tg, R=Rp, mode=mode, symmetric=sym, a_range=(lo, hi), order="integral_first")
             # nothing outside this range's share is written
             parts += Rp
         assert rel(parts.cpu().numpy(), full.cpu().numpy()) < 1e-14
