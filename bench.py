@@ -182,10 +182,11 @@ def cpu_model() -> str:
 
 
 def traffic_record():
-    """Per-launch DRAM bytes of the tensor-core GEMM from the committed ncu summary, if the
-    kernel source is unchanged since it was captured (else None)."""
+    """DRAM bytes over algorithmic bytes of the tensor-core GEMM, from the committed summary of one
+    small-case ncu capture (profiles/gemm_tc_traffic.json), if the kernel source is unchanged since
+    it was captured (else None)."""
     import hashlib
-    p = os.path.join(ROOT, "profiles", "traffic.json")
+    p = os.path.join(ROOT, "profiles", "gemm_tc_traffic.json")
     if not os.path.exists(p):
         return None
     rec = json.load(open(p))
@@ -280,14 +281,20 @@ def run_ours(a):
     tc = [k for k in prof if k.endswith("_tc")]
     tc_ms = sum(prof[k]["ms"] for k in tc)
     tc_fl = sum(prof[k]["flops"] for k in tc)
+    tc_by = sum(prof[k]["bytes"] for k in tc)
     tc_n = sum(prof[k]["launches"] for k in tc)
     pk, pk_src = peaks()
     peak = pk.get("bf16_tflops_sustained", pk["bf16_tflops"])
     achieved = tc_fl / (tc_ms / 1e3) / 1e12 if tc_ms > 0 else None
     tr = traffic_record()
+    alg_bytes = tc_by / max(tc_n, 1)
     roofline = {"kernel": "gemm_tc_kernel<bf16>", "bound": "tensor", "achieved": achieved, "peak": peak,
                 "unit": "TFLOP/s", "frac": (achieved / peak) if achieved else None,
-                "traffic": tr["bytes_per_launch"] if tr else None,
+                "traffic": tr["ratio"] * alg_bytes if tr else None,
+                "algorithmic_bytes_per_launch": alg_bytes,
+                "traffic_source": (f"ncu dram__bytes_read+write of one small-case launch ({tr['launch']}): "
+                                   f"{tr['ratio']:.2f} x its algorithmic bytes, applied to this workload's "
+                                   "algorithmic bytes per launch") if tr else None,
                 "peak_source": f"{pk_src} bf16_tflops_sustained (kernel timed inside a long step), of measured"
                                if pk_src == "measured" else "fallback 1.7 PFLOP/s sustained, of fallback",
                 "launches": tc_n, "flops_per_launch": tc_fl / max(tc_n, 1), "ms_per_launch": tc_ms / max(tc_n, 1),
@@ -373,7 +380,7 @@ def extras(a, out, o, v, n, mode, L_np, t2_np, Lg, tg, R, ws, E_e2e, value, dev,
 
     pk, _ = peaks()
     probed = {}
-    for name in ("dmma", "dfma", "tc_bf16", "tc_tf32"):
+    for name in ("dmma", "dfma", "tc_bf16", "tc_tf32", "imma"):
         try:
             probed[name] = B.peak_probe(name, device=dev)
         except Exception as e:  # noqa: BLE001 - reported, the main figures stand

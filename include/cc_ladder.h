@@ -67,14 +67,16 @@ enum cc_status {
 enum cc_precision {
     CC_FP64 = 0,       /* FP64 tensor-core MMA (DMMA), FP64 accumulation              */
     CC_OZAKI_BF16 = 1, /* FP64 emulated by split BF16 integer slices (Ozaki scheme) on
-                          tcgen05 tensor cores, FP32 accumulation of each slice-product level,
-                          exact int64 / FP64 recombination.  A level's FP32 sum is exact while its
-                          partial sums stay below 2^24: for any input when the contraction length
-                          is at most 4096 / (level + 1), and for all but adversarially aligned
-                          inputs beyond that (row-max scaling keeps typical sums near 2^17..2^22).
-                          The integral builds split contractions longer than 6144 across CTAs
-                          with exact int64 partial sums, so their diagonal integrals (ac|ac), whose
-                          lower-digit squares add with one sign, stay exact for any n_chol. */
+                          tcgen05 tensor cores: each operand row is scaled by a power of two and
+                          rounded once to a 42-bit integer cut into 6 balanced 7-bit digits (2..8
+                          slices selectable); the slice products of each level are summed in FP32
+                          on the tensor cores and drained to exact int64 at most every
+                          4096 / (products in the level) contraction elements, so every FP32 sum
+                          stays an exact integer below 2^24 for ANY input (sign-aligned data,
+                          constant matrices, Gram diagonals included); levels are recombined in
+                          int64 and converted to FP64 once.  Error: the 42-bit rounding of the
+                          inputs and the dropped levels, about 1e-11 relative.  NaN / Inf inputs
+                          give CC_ERR_NONFINITE. */
     CC_OZAKI_INT8 = 2, /* INT8-slice emulation: tcgen05 has no kind::i8 on sm_103a;
                           always returns CC_ERR_UNSUPPORTED                           */
     CC_TF32 = 3,       /* TF32 inputs, FP32 accumulation per K-chunk, FP64 across chunks */
@@ -284,9 +286,7 @@ void cc_ladder_set_wait_limit_ns(unsigned long long ns);
  * in the arithmetic of `mode` (CC_FP64: DMMA; CC_OZAKI_BF16: split BF16 slices on tcgen05 with
  * FP64 recombination; CC_TF32 / CC_BF16: one rounded copy, FP32 accumulation per K-chunk).
  * accumulate != 0 adds into C.  Workspace from cc_ladder_gemm_workspace_size.
- * CC_OZAKI_BF16 here does not split K for exactness: where a row of A equals a row of B (the
- * diagonal of a Gram matrix A A^T), the squares of the lower digits add with one sign and those
- * entries lose exactness beyond K of about 12 000 (a few 1e-10 relative). */
+ * CC_OZAKI_BF16 is exact in its FP32 level sums for any K and any input (see cc_precision). */
 int cc_ladder_gemm_workspace_size(int mode, int M, int N, int K, int slices, size_t* bytes);
 int cc_ladder_gemm(int mode, int M, int N, int K, const double* A, int lda, const double* B, int ldb, double* C,
                    int ldc, int accumulate, int slices, void* workspace, size_t ws_bytes, void* stream);
@@ -294,7 +294,7 @@ int cc_ladder_gemm(int mode, int M, int N, int K, const double* A, int lda, cons
 /* Tracing.  cc_ladder_profile_enable(1) resets and starts per-phase timing: every phase of
  * every later call records CUDA events on its stream.  cc_ladder_profile_read synchronises
  * those events and fills up to max_entries totals (phase name, launches, milliseconds,
- * tensor-core or FP64 flops issued); it returns the number of phases.  Profiling adds two
+ * tensor-core or FP64 flops issued, algorithmic bytes); it returns the number of phases.  Profiling adds two
  * events per phase and is off by default.  cc_ladder_launch_count is the number of kernels
  * the library has launched in this process.  Every phase is also an NVTX range of the same name
  * (visible in timeline profilers; free when none is attached), and with the environment variable
@@ -304,6 +304,8 @@ typedef struct cc_ladder_profile_entry {
     int launches;
     double ms;
     double flops;
+    double bytes;   /* algorithmic DRAM bytes of the slice GEMMs: every operand slice read once and
+                       the output written once (read too when accumulated); 0 for other phases */
 } cc_ladder_profile_entry;
 void cc_ladder_profile_enable(int on);
 int cc_ladder_profile_read(cc_ladder_profile_entry* out, int max_entries);
@@ -318,10 +320,12 @@ long long cc_ladder_launch_count(void);
  *   CC_PROBE_TC_BF16  tcgen05.mma kind::f16, BF16 operands in shared memory, M=128 N=256 K=16,
  *                     one issuing thread per SM (the emulated-FP64 and BF16 modes)
  *   CC_PROBE_TC_TF32  tcgen05.mma kind::tf32, M=128 N=256 K=8 (the TF32 mode)
+ *   CC_PROBE_IMMA     mma.sync.m16n8k32.s8 from registers (TOP/s): legacy INT8 MMA, the only INT8
+ *                     tensor-core form sm_103a assembles (ptxas rejects tcgen05 kind::i8 there)
  * iters (1 .. 2^24): loop trips per thread (tensor-core probes: groups of four MMAs).  The
  * tensor-core probes' wait for their last MMAs is bounded (2 s, CC_ERR_DEVICE_TIMEOUT).
  * Allocates no device memory. */
-enum cc_probe { CC_PROBE_DMMA = 1, CC_PROBE_DFMA = 2, CC_PROBE_TC_BF16 = 3, CC_PROBE_TC_TF32 = 4 };
+enum cc_probe { CC_PROBE_DMMA = 1, CC_PROBE_DFMA = 2, CC_PROBE_TC_BF16 = 3, CC_PROBE_TC_TF32 = 4, CC_PROBE_IMMA = 5 };
 int cc_ladder_peak_probe(int which, int iters, void* stream, double* tflops);
 
 /* Static description of a status code. */

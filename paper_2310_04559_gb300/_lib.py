@@ -48,7 +48,8 @@ class Plan(ctypes.Structure):
 
 class ProfileEntry(ctypes.Structure):
     """struct cc_ladder_profile_entry"""
-    _fields_ = [("name", ctypes.c_char * 32), ("launches", _i), ("ms", ctypes.c_double), ("flops", ctypes.c_double)]
+    _fields_ = [("name", ctypes.c_char * 32), ("launches", _i), ("ms", ctypes.c_double), ("flops", ctypes.c_double),
+                ("bytes", ctypes.c_double)]
 
 
 class LadderError(RuntimeError):
@@ -68,7 +69,7 @@ SYMBOLS = [
     "cc_ladder_autotune", "cc_ladder_partition", "cc_ladder_peak_probe", "cc_ladder_term_workspace_size", "cc_ladder_term", "cc_ladder_tijkl", "cc_ladder_tijbk",
 ]
 TERMS = {"ijkl": 1, "ijbk": 2}
-PROBES = {"dmma": 1, "dfma": 2, "tc_bf16": 3, "tc_tf32": 4}
+PROBES = {"dmma": 1, "dfma": 2, "tc_bf16": 3, "tc_tf32": 4, "imma": 5}
 
 
 def lib_path() -> str:

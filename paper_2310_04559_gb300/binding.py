@@ -295,9 +295,9 @@ def gemm(A, B, mode="ozaki_bf16", C=None, accumulate=False, slices=0):
 
 def peak_probe(which, iters=0, device=None) -> float:
     """Measured peak rate (TFLOP/s of the whole GPU) of one arithmetic unit: "dmma", "dfma",
-    "tc_bf16" or "tc_tf32" (see cc_ladder_peak_probe)."""
+    "tc_bf16", "tc_tf32" or "imma" (TOP/s; see cc_ladder_peak_probe)."""
     lib = _lib.load()
-    default_iters = {"dmma": 4096, "dfma": 16384, "tc_bf16": 20000, "tc_tf32": 10000}
+    default_iters = {"dmma": 4096, "dfma": 16384, "tc_bf16": 20000, "tc_tf32": 10000, "imma": 4096}
     out = ctypes.c_double()
     _lib.check(lib.cc_ladder_peak_probe(_lib.PROBES[which], int(iters or default_iters[which]), _stream(device),
                                         ctypes.byref(out)), "cc_ladder_peak_probe")
@@ -309,13 +309,13 @@ def profile_enable(on=True):
 
 
 def profile_read() -> dict:
-    """{phase: {"launches", "ms", "flops"}} accumulated since profile_enable(True)."""
+    """{phase: {"launches", "ms", "flops", "bytes"}} accumulated since profile_enable(True)."""
     lib = _lib.load()
     n = lib.cc_ladder_profile_read(None, 0)
     arr = (_lib.ProfileEntry * max(n, 1))()
     n = lib.cc_ladder_profile_read(arr, n)
-    return {arr[i].name.decode(): {"launches": arr[i].launches, "ms": arr[i].ms, "flops": arr[i].flops}
-            for i in range(n)}
+    return {arr[i].name.decode(): {"launches": arr[i].launches, "ms": arr[i].ms, "flops": arr[i].flops,
+                                   "bytes": arr[i].bytes} for i in range(n)}
 
 
 def launch_count() -> int:

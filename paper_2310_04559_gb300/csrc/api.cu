@@ -460,8 +460,8 @@ double tc_products(const Ctx& c) { return c.mode == CC_OZAKI_BF16 ? c.s * (c.s +
 
 // Output elements of an M x N slice GEMM that lie in tiles the triangular skip keeps
 // (a(m) = m / tri, b(n) = n / tri; a tile goes when b < a for all its elements).
-// Tile edges TM x TN: 256 x 128 (a CTA pair) in gemm_tc.cu, 64 x 64 in gemm_f64.cu.
-double tri_elems(long long M, long long N, long long tri, long long TM = 256, long long TN = 128)
+// Tile edges TM x TN: 128 x 128 in gemm_tc.cu, 64 x 64 in gemm_f64.cu.
+double tri_elems(long long M, long long N, long long tri, long long TM = 128, long long TN = 128)
 {
     if (tri <= 0) return (double)M * N;
     double e = 0.0;
@@ -496,11 +496,16 @@ int run_tc(const char* name, const Ctx& c, int M, int N, int K, const Operand& A
            long long rowB0, const OutDesc& out, int* status, cudaStream_t st, bool intermediate = false,
            long long tri = 0, bool add_int64 = false)
 {
-    ProfScope ps(name, st, 2.0 * tri_elems(M, N, tri) * K * tc_products(c));
-    // C = A B^T and C^T = B A^T are the same GEMM: take the orientation whose 256 x 128 pair
-    // tiles pad the output least (not with the triangular skip, which is one-sided)
-    auto padded = [](long long m, long long n) { return (double)((m + 255) / 256 * 256) * ((n + 127) / 128 * 128); };
-    const bool swap = tri == 0 && padded(N, M) < padded(M, N);
+    // algorithmic bytes: every slice of both operands read once, the kept output written once
+    // (8 bytes per element; read as well when accumulated)
+    const double out_el = tri_elems(M, N, tri);
+    const int opb = c.mode == CC_TF32 ? 4 : 2;
+    const double bytes = (double)opb * c.s * ((double)M + N) * K + out_el * 8.0 * (out.accumulate ? 2 : 1);
+    ProfScope ps(name, st, 2.0 * out_el * K * tc_products(c), bytes);
+    // C = A B^T and C^T = B A^T are the same GEMM; the tiles are square (128 x 128), so the
+    // orientation changes no padding: the longer operand is kept as A, whose rows are the
+    // slowest-moving index of the tile raster (not with the triangular skip, which is one-sided)
+    const bool swap = tri == 0 && N > M;
     const Operand& Aop = swap ? B : A;
     const Operand& Bop = swap ? A : B;
     OutDesc o = out;
@@ -528,13 +533,13 @@ int run_tc(const char* name, const Ctx& c, int M, int N, int K, const Operand& A
         }
         g.epi = intermediate ? (add_int64 ? EPI_FIXED64_ADD : EPI_FIXED64_RED) : EPI_FIXED64;
         g.fixF = kFixF;
-        // Few tiles of long K: split K over pairs of CTAs so that the items fill whole waves of
+        // Few tiles of long K: split K over CTAs so that the items fill whole waves of
         // the device (int64 adds into a zeroed output, then one conversion pass for final outputs)
         if (!o.accumulate) {
-            const long long tiles = (long long)((M + 255) / 256) * ((N + 127) / 128);
-            const int npairs = std::max(1, device_sm_count() / 2);
+            const long long tiles = (long long)((M + 127) / 128) * ((N + 127) / 128);
+            const int nsm = std::max(1, device_sm_count());
             auto eff = [&](int S) {
-                const double w = (double)tiles * S / npairs;
+                const double w = (double)tiles * S / nsm;
                 return w / std::ceil(w);
             };
             int best = 1;
@@ -616,9 +621,11 @@ int fwd_packed(const Ctx& c, const cc_ladder_args* a, const double* Lsrc, const 
             CC_CU(cudaEventCreateWithFlags(&sm.freed[b], cudaEventDisableTiming));
         }
     }
-    // consume(buf, P0, Pq): enqueue on st the work that reads chunk [P0, P0 + Pq) of L in buf
+    // consume(buf, P0, Pq): enqueue on st the work that reads chunk [P0, P0 + Pq) of L in buf.
+    // The chunk counter runs on across calls, so the first copies of a pass still wait for the
+    // last readers of their buffers in the pass before.
+    long long q = 0;
     auto stream_L = [&](auto&& consume) -> int {
-        long long q = 0;
         for (long long P0 = 0; P0 < n; P0 += c.PC, ++q) {
             const long long Pq = std::min<long long>(c.PC, n - P0);
             const int b = (int)(q & 1);

@@ -200,7 +200,7 @@ void count_launch(int n = 1);
 // Records CUDA events around a phase on `s` when profiling is enabled.
 class ProfScope {
   public:
-    ProfScope(const char* name, cudaStream_t s, double flops = 0.0);
+    ProfScope(const char* name, cudaStream_t s, double flops = 0.0, double bytes = 0.0);
     ~ProfScope();
     ProfScope(const ProfScope&) = delete;
     ProfScope& operator=(const ProfScope&) = delete;
@@ -208,7 +208,7 @@ class ProfScope {
   private:
     const char* name_;
     cudaStream_t s_;
-    double flops_;
+    double flops_, bytes_;
     void* e0_;
 };
 

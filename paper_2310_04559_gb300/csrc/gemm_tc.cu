@@ -4,12 +4,13 @@
 //   C[rmap(m) + cmap(n)] (= or +=) sum_levels 2^(eA[m] + eB[n] + base - beta*level)
 //                                  * sum_{i+j=level} A_i(m,:) . B_j(n,:)
 //
-// Operands are K-major slice stacks D[slice][row][pitch].  A pair of CTAs (a
-// cluster of two SMs) owns a 256 x 128 output tile: each CTA stages its 128 rows
-// of A and 64 of the tile's 128 rows of B, and the leader CTA issues
-// tcgen05.mma.cta_group::2 (M = 256, N = 128), which reads both CTAs' shared
-// memory and accumulates 128 x 128 FP32 per CTA in its tensor memory.  The
-// kernel is persistent: every pair walks a strided list of (tile, K-split) items.
+// Operands are K-major slice stacks D[slice][row][pitch].  One CTA per SM owns a
+// 128 x 128 output tile at a time and issues tcgen05.mma.cta_group::1 (M = N = 128, 64 clocks
+// of the tensor pipe each) into its tensor memory.  The kernel is persistent: every CTA walks a
+// strided list of (tile, K-split) items.  (Pairs of SMs on one 256-row tile, cta_group::2, were
+// measured slower here: every slot of the operand rings then waits for handshakes between the
+// two SMs, which cut the copy throughput per SM to about a third, and this GEMM streams about one
+// operand tile per slice product.)
 //
 // Passes.  The slice-product levels L (products A_i B_j with i + j = L) are
 // processed in groups of at most two; a "pass" is one group over one K-chunk, and
@@ -36,18 +37,16 @@
 // i = hi..lo through a FIFO, so B_j meets every A_i with i + j in the pass while
 // A_i lives only until its last partner has passed.
 //
-// Roles (384 threads, three warpgroups): warp 0 TMA producer (both CTAs; the
-// copies of both complete on the leader's barriers, cp.async.bulk.tensor
-// .cta_group::2), warps 1-2 MMA issuers in the leader (one per level of a pass;
-// warp 1 of each CTA allocates TMEM), warp 3 idle, warps 4-11 epilogue (two per
-// TMEM lane quarter).  setmaxnreg moves registers from warpgroup 0 to the
-// epilogue warpgroups, which hold the running sums.  No multicast instruction is
-// used: the leader signals the follower's barriers with separate commits.
+// Roles (512 threads, four warpgroups): warps 0, 3 (A slices) and 4, 5 (B slices) are TMA
+// producers, each issuing every other copy of its operand -- one thread keeps only about one
+// copy in flight per 0.3 us (measured), fewer than the tensor pipe consumes.  Warps 1-2 issue
+// the MMAs (one per level of a pass; warp 1 allocates TMEM), warps 6-7 idle, warps 8-15 are
+// the epilogue (two per TMEM lane quarter).  setmaxnreg moves registers from warpgroups 0-1 to
+// the epilogue warpgroups, which hold the running sums.
 //
 // Every mbarrier wait is bounded (globaltimer); on expiry the CTA raises a
 // shared abort flag and the device status word, drains what it has in flight
-// (with a fixed bound), and both CTAs meet at the final cluster barrier, free
-// TMEM and exit.
+// (with a fixed bound), frees TMEM and exits.
 #include <cuda.h>
 #include <cudaTypedefs.h>
 #include <cuda_runtime.h>
@@ -61,34 +60,32 @@
 namespace cc {
 namespace {
 
-constexpr int BM = 128;                        // output rows per CTA (a pair covers 2 BM)
-constexpr int BN = 128;                        // output columns per pair tile
-constexpr int BNH = BN / 2;                    // B rows each CTA of a pair stages
+constexpr int BM = 128;                        // output rows per tile
+constexpr int BN = 128;                        // output columns per tile
 constexpr int ROW_BYTES = 128;                 // K bytes per tile row: one 128-byte swizzle atom
 constexpr int A_TILE = BM * ROW_BYTES;         // 16 KB per A slice tile
-constexpr int B_TILE = BNH * ROW_BYTES;        // 8 KB per half B slice tile
-constexpr int NA = 8, NB = 8;                  // A FIFO and B ring slots
+constexpr int B_TILE = BN * ROW_BYTES;         // 16 KB per B slice tile
+constexpr int NA = 6, NB = 6;                  // A FIFO and B ring slots
 constexpr int TILE_SMEM = NA * A_TILE + NB * B_TILE;  // 192 KB
 constexpr int MAX_SLICES = 8;
 constexpr int ISSUERS = 2;                     // MMA-issuing warps (one per level of a pass)
 constexpr int EPI_WARPS = 8;                   // two per TMEM lane quarter
 constexpr int EPI_THREADS = 32 * EPI_WARPS;
-constexpr int THREADS = 32 * 4 + EPI_THREADS;  // 384
+constexpr int THREADS = 32 * 8 + EPI_THREADS;  // 512: producers and MMA issuers, then the epilogue
 constexpr int TMEM_COLS = 512;                 // 2 buffers x 2 levels x BN columns
 constexpr int COLS_PER_THREAD = BN / 2;        // 64 accumulator columns per epilogue thread
-// setmaxnreg split of the 384 x 168 registers of the launch: warpgroup 0 keeps 88,
-// the two epilogue warpgroups (running sums) get 208: 128 * 88 + 256 * 208 = 384 * 168.
-constexpr int REG_LAUNCH = 168, REG_LOW = 88, REG_HIGH = 208;
-static_assert(128 * REG_LOW + 256 * REG_HIGH <= THREADS * REG_LAUNCH, "register split exceeds the launch's share");
+// setmaxnreg split of the 512 x 128 registers of the launch: warpgroups 0-1 (producers, MMA
+// issuers) keep 64, the two epilogue warpgroups (running sums) get 192: 256 * 64 + 256 * 192 = 512 * 128.
+constexpr int REG_LAUNCH = 128, REG_LOW = 64, REG_HIGH = 192;
+static_assert(256 * REG_LOW + 256 * REG_HIGH <= THREADS * REG_LAUNCH, "register split exceeds the launch's share");
 constexpr unsigned long long kDrainLimitNs = 1000000000ull;  // bound on the abort-path drains
-constexpr unsigned long long kLandNs = 10000000ull;          // follower's wait for its copies after an abort
 
 enum OutKind { OUT_F64 = 0, OUT_I64 = 1, OUT_I64_RED = 2 };
 
 struct SmemCtl {
-    unsigned long long afull[NA], aempty[NA];  // afull / bfull: used in the leader only
+    unsigned long long afull[NA], aempty[NA];
     unsigned long long bfull[NB], bempty[NB];
-    unsigned long long tfull[2], tempty[2];    // tempty: used in the leader only
+    unsigned long long tfull[2], tempty[2];
     unsigned long long drain[ISSUERS];
     unsigned int tmem_base;
     volatile int abort;
@@ -121,26 +118,6 @@ __device__ __forceinline__ unsigned long long gtime()
     unsigned long long t;
     asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
     return t;
-}
-
-__device__ __forceinline__ uint32_t cluster_rank()
-{
-    uint32_t r;
-    asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
-    return r;
-}
-
-// Shared::cluster address of the object at the same offset in CTA `rank` of the cluster.
-__device__ __forceinline__ uint32_t peer_addr(uint32_t local, uint32_t rank)
-{
-    uint32_t r;
-    asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(local), "r"(rank));
-    return r;
-}
-
-__device__ __forceinline__ void cluster_sync()
-{
-    asm volatile("barrier.cluster.arrive.release.aligned;\nbarrier.cluster.wait.acquire.aligned;" ::: "memory");
 }
 
 __device__ __forceinline__ void mbar_init(unsigned long long* b, unsigned count)
@@ -199,20 +176,16 @@ __device__ __forceinline__ void mbar_expect_tx(unsigned long long* b, uint32_t b
     asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(b)), "r"(bytes) : "memory");
 }
 
-// Arrive on the barrier at shared::cluster address `addr` (this CTA's or the peer's).
-__device__ __forceinline__ void mbar_arrive_cluster(uint32_t addr)
+__device__ __forceinline__ void mbar_arrive(unsigned long long* b)
 {
-    asm volatile("mbarrier.arrive.release.cluster.shared::cluster.b64 _, [%0];" ::"r"(addr) : "memory");
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(b)) : "memory");
 }
 
-// 2-CTA tile load: lands in this CTA's shared memory, completes on the barrier at
-// shared::cluster address `bar` (the leader's).
-__device__ __forceinline__ void tma_load_3d_pair(void* dst, const CUtensorMap* map, uint32_t bar, int x, int y, int z)
+__device__ __forceinline__ void tma_load_3d(void* dst, const CUtensorMap* map, unsigned long long* bar, int x, int y, int z)
 {
     asm volatile(
-        "cp.async.bulk.tensor.3d.cta_group::2.shared::cluster.global.mbarrier::complete_tx::bytes"
-        " [%0], [%1, {%2, %3, %4}], [%5];"
-        ::"r"(smem_u32(dst)), "l"((unsigned long long)map), "r"(x), "r"(y), "r"(z), "r"(bar)
+        "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], [%5];"
+        ::"r"(smem_u32(dst)), "l"((unsigned long long)map), "r"(x), "r"(y), "r"(z), "r"(smem_u32(bar))
         : "memory");
 }
 
@@ -231,49 +204,40 @@ __device__ __forceinline__ unsigned long long smem_desc(const void* p)
 }
 
 // Instruction descriptor: FP32 accumulate, A/B format (1 = BF16, 2 = TF32),
-// both K-major, N = BN, M = 2 BM (the CTA pair).
+// both K-major, N = BN, M = BM.
 template <int KIND>
 __device__ __forceinline__ uint32_t instr_desc()
 {
     const uint32_t fmt = KIND == TC_BF16 ? 1u : 2u;
-    return (1u << 4) | (fmt << 7) | (fmt << 10) | ((uint32_t)(BN >> 3) << 17) | ((uint32_t)((2 * BM) >> 4) << 24);
+    return (1u << 4) | (fmt << 7) | (fmt << 10) | ((uint32_t)(BN >> 3) << 17) | ((uint32_t)(BM >> 4) << 24);
 }
 
 template <int KIND>
-__device__ __forceinline__ void mma_pair(uint32_t tmem_d, unsigned long long adesc, unsigned long long bdesc,
+__device__ __forceinline__ void mma(uint32_t tmem_d, unsigned long long adesc, unsigned long long bdesc,
                                          uint32_t idesc, uint32_t accumulate)
 {
     if (KIND == TC_BF16) {
         asm volatile(
             "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
-            " tcgen05.mma.cta_group::2.kind::f16 [%0], %1, %2, %3, p;\n}\n"
+            " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n"
             ::"r"(tmem_d), "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate));
     } else {
         asm volatile(
             "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
-            " tcgen05.mma.cta_group::2.kind::tf32 [%0], %1, %2, %3, p;\n}\n"
+            " tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n"
             ::"r"(tmem_d), "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate));
     }
 }
 
-// Arrive on the barrier at shared::cluster address `bar` once this thread's prior MMAs complete.
-__device__ __forceinline__ void mma_commit(uint32_t bar)
+// Arrive on `bar` once this thread's prior MMAs complete.
+__device__ __forceinline__ void mma_commit(unsigned long long* bar)
 {
-    asm volatile("tcgen05.commit.cta_group::2.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar) : "memory");
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
+                 : "memory");
 }
 
 __device__ __forceinline__ void fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
-
-// 32 lanes x 16 columns of TMEM into registers (no wait: pair with tmem_wait_ld).
-__device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&r)[16])
-{
-    asm volatile(
-        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
-        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
-          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
-        : "r"(taddr));
-}
 
 // 32 lanes x 8 columns.
 __device__ __forceinline__ void tmem_ld8(uint32_t taddr, uint32_t (&r)[8])
@@ -326,7 +290,7 @@ __device__ __forceinline__ Item item_of(const Params& p, int i)
     const int gm = min(p.tiles_m - first_m, p.group_m);
     Item it;
     it.split = i / ntiles;
-    it.m0 = (first_m + (t % per_group) % gm) * (2 * BM);
+    it.m0 = (first_m + (t % per_group) % gm) * BM;
     it.n0 = ((t % per_group) / gm) * BN;
     // triangular skip: every element of the tile has b(n) < a(m)
     it.skip = false;
@@ -383,44 +347,60 @@ gemm_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
 
     constexpr int KSTEP = KIND == TC_BF16 ? 64 : 32;  // K elements per 128-byte row
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const uint32_t rank = cluster_rank();
-    const bool leader = rank == 0;
-    const int pair = (int)(blockIdx.x >> 1), npairs = (int)(gridDim.x >> 1);
+    const int cta = (int)blockIdx.x, nctas = (int)gridDim.x;
 
     if (threadIdx.x == 0) {
         for (int s = 0; s < NA; ++s) { mbar_init(&ctl->afull[s], 1); mbar_init(&ctl->aempty[s], ISSUERS); }
         for (int s = 0; s < NB; ++s) { mbar_init(&ctl->bfull[s], 1); mbar_init(&ctl->bempty[s], ISSUERS); }
-        for (int b = 0; b < 2; ++b) { mbar_init(&ctl->tfull[b], ISSUERS); mbar_init(&ctl->tempty[b], 2 * EPI_WARPS); }
+        for (int b = 0; b < 2; ++b) { mbar_init(&ctl->tfull[b], ISSUERS); mbar_init(&ctl->tempty[b], EPI_WARPS); }
         for (int q = 0; q < ISSUERS; ++q) mbar_init(&ctl->drain[q], 1);
         ctl->abort = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     if (warp == 1) {
-        asm volatile("tcgen05.alloc.cta_group::2.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&ctl->tmem_base)),
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&ctl->tmem_base)),
                      "r"(TMEM_COLS));
-        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::2.sync.aligned;");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
     }
     fence_before();
     __syncthreads();
-    cluster_sync();  // the peer's barriers are initialised before any copy or commit reaches them
     fence_after();
     const uint32_t tmem = ctl->tmem_base;
 
-    if (warp < 4) {
+    if (warp < 8) {
         asm volatile("setmaxnreg.dec.sync.aligned.u32 %0;" ::"n"(REG_LOW));
-        if (warp == 0 && lane == 0) {
-            // -------------------------------------------------------- producer
-            // Per K-step: for j = lo..hi, first the A tiles (in order i = hi..lo) down to
-            // the lowest i that B_j needs, then B_j.  Both CTAs load their halves into the
-            // same slots; the copies complete on the leader's full barriers, where the
-            // leader expects the bytes of both.
-            asm volatile("prefetch.tensormap [%0];" ::"l"((unsigned long long)&tmA) : "memory");
-            asm volatile("prefetch.tensormap [%0];" ::"l"((unsigned long long)&tmB) : "memory");
-            long long a_issued = 0, b_issued = 0;
+        const int prod = warp == 0 ? 0 : warp == 3 ? 1 : warp == 4 ? 2 : warp == 5 ? 3 : -1;
+        if (prod >= 0 && lane == 0) {
+            // -------------------------------------------------------- producers
+            // Four producer threads (warps 0, 3: A slices; 4, 5: B slices), each issuing every
+            // other copy of its operand: one thread keeps only about one copy in flight per 0.3 us,
+            // which alone would starve the tensor pipe.  All walk the same sequence -- per K-step,
+            // for j = lo..hi, the A tiles (i = hi..lo) down to the lowest i that B_j needs, then
+            // B_j -- and count every copy of their operand.
+            const bool isA = prod < 2;
+            const long long mine = prod & 1;
+            const CUtensorMap* map = isA ? &tmA : &tmB;
+            asm volatile("prefetch.tensormap [%0];" ::"l"((unsigned long long)map) : "memory");
+            const int NS = isA ? NA : NB;
+            const uint32_t tile = isA ? A_TILE : B_TILE;
+            unsigned char* ring = isA ? aring : bring;
+            unsigned long long* full = isA ? ctl->afull : ctl->bfull;
+            unsigned long long* empty = isA ? ctl->aempty : ctl->bempty;
+            long long issued = 0;  // copies of this operand in the sequence so far (all producers')
             bool ok = true;
-            for (int item = pair; item < p.nitems && ok; item += npairs) {
+            auto load = [&](int kb, int row, int slice) -> bool {
+                const long long u = issued++;
+                if ((u & 1) != mine) return true;
+                const int s = (int)(u % NS);
+                if (!wait_fast(&empty[s], (uint32_t)(((u / NS) & 1) ^ 1), ctl, p)) return false;
+                mbar_expect_tx(&full[s], tile);
+                tma_load_3d(ring + s * tile, map, &full[s], kb, row, slice);
+                return true;
+            };
+            for (int item = cta; item < p.nitems && ok; item += nctas) {
                 const Item w = item_of(p, item);
                 if (w.skip) continue;
+                const int rowA = (int)(p.rowA0 + w.m0), rowB = (int)(p.rowB0 + w.n0);
                 PassIter it;
                 it.begin(p, w.split);
                 do {
@@ -431,74 +411,38 @@ gemm_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
                         int a_here = 0;
                         for (int j = lo; j <= hi && ok; ++j) {
                             const int imin = L1 - j > lo ? L1 - j : lo;
-                            while (a_here < hi - imin + 1) {
-                                const int as = (int)(a_issued % NA);
-                                const uint32_t par = (uint32_t)(((a_issued / NA) & 1) ^ 1);
-                                if (!wait_fast(&ctl->aempty[as], par, ctl, p)) { ok = false; break; }
-                                if (leader) mbar_expect_tx(&ctl->afull[as], 2 * A_TILE);
-                                tma_load_3d_pair(aring + as * A_TILE, &tmA, peer_addr(smem_u32(&ctl->afull[as]), 0),
-                                                 kb, (int)(p.rowA0 + w.m0 + (int)rank * BM), hi - a_here);
-                                ++a_issued;
-                                ++a_here;
-                            }
-                            if (!ok) break;
-                            const int bs = (int)(b_issued % NB);
-                            const uint32_t bpar = (uint32_t)(((b_issued / NB) & 1) ^ 1);
-                            if (!wait_fast(&ctl->bempty[bs], bpar, ctl, p)) { ok = false; break; }
-                            if (leader) mbar_expect_tx(&ctl->bfull[bs], 2 * B_TILE);
-                            tma_load_3d_pair(bring + bs * B_TILE, &tmB, peer_addr(smem_u32(&ctl->bfull[bs]), 0), kb,
-                                             (int)(p.rowB0 + w.n0 + (int)rank * BNH), j);
-                            ++b_issued;
+                            for (; a_here < hi - imin + 1 && ok; ++a_here)
+                                if (isA) ok = load(kb, rowA, hi - a_here);
+                            if (ok && !isA) ok = load(kb, rowB, j);
                         }
                     }
                 } while (ok && it.next(p));
             }
             if (ok) {
-                // tail: every slot's last use released, so no commit of the leader still
-                // targets this CTA's barriers when it leaves
-                for (long long q = 1; q <= (a_issued < NA ? a_issued : NA) && ok; ++q) {
-                    const long long u = a_issued - q;
-                    ok = wait_fast(&ctl->aempty[u % NA], (uint32_t)((u / NA) & 1), ctl, p);
-                }
-                for (long long q = 1; q <= (b_issued < NB ? b_issued : NB) && ok; ++q) {
-                    const long long u = b_issued - q;
-                    ok = wait_fast(&ctl->bempty[u % NB], (uint32_t)((u / NB) & 1), ctl, p);
-                }
+                // tail: the last use of every slot this producer filled is released, so no commit
+                // still targets the barriers when the CTA leaves
+                for (long long u = issued - 1; u >= 0 && u >= issued - NS && ok; --u)
+                    if ((u & 1) == mine) ok = wait_fast(&empty[u % NS], (uint32_t)((u / NS) & 1), ctl, p);
             }
             if (!ok) {
-                if (leader) {
-                    // the newest copy into each slot may still be in flight
-                    for (long long q = 1; q <= (a_issued < NA ? a_issued : NA); ++q) {
-                        const long long u = a_issued - q;
-                        mbar_drain_wait(&ctl->afull[u % NA], (uint32_t)((u / NA) & 1), p.status);
-                    }
-                    for (long long q = 1; q <= (b_issued < NB ? b_issued : NB); ++q) {
-                        const long long u = b_issued - q;
-                        mbar_drain_wait(&ctl->bfull[u % NB], (uint32_t)((u / NB) & 1), p.status);
-                    }
-                } else {
-                    // the follower's copies complete on the leader's barriers: give them time to land
-                    const unsigned long long t0 = gtime();
-                    while (gtime() - t0 < kLandNs) {}
-                }
+                // the newest copy into each of its slots may still be in flight
+                for (long long u = issued - 1; u >= 0 && u >= issued - NS; --u)
+                    if ((u & 1) == mine) mbar_drain_wait(&full[u % NS], (uint32_t)((u / NS) & 1), p.status);
             }
-        } else if (leader && (warp == 1 || warp == 2) && lane == 0) {
+        } else if ((warp == 1 || warp == 2) && lane == 0) {
             // ------------------------------------------------------------ MMA
             // Issuer `me` owns level L1 + me of a two-level pass (columns me * BN of the
             // pass's buffer); in a one-level pass issuer 0 does all MMAs and issuer 1 only
             // paces, releases and commits.  Both walk the same tile sequence, wait for the
-            // same tiles and release every slot in both CTAs (arrival count 2 each).
+            // same tiles and release every slot (arrival count 2 each).
             const int me = warp - 1;
             const uint32_t idesc = instr_desc<KIND>();
             // slot q's descriptor = slot 0's + q * tile_bytes / 16 in the start-address field
             // (shared addresses stay below 256 KB, so the 14-bit field never carries over)
             const unsigned long long adesc0 = smem_desc(aring), bdesc0 = smem_desc(bring);
-            const uint32_t aempty0 = smem_u32(&ctl->aempty[0]), bempty0 = smem_u32(&ctl->bempty[0]);
-            const uint32_t aempty1 = peer_addr(aempty0, 1), bempty1 = peer_addr(bempty0, 1);
-            const uint32_t tfull0 = smem_u32(&ctl->tfull[0]), tfull1 = peer_addr(tfull0, 1);
             uint32_t a_used = 0, b_used = 0, npass = 0;
             bool ok = true, any = false;
-            for (int item = pair; item < p.nitems && ok; item += npairs) {
+            for (int item = cta; item < p.nitems && ok; item += nctas) {
                 const Item w = item_of(p, item);
                 if (w.skip) continue;
                 PassIter it;
@@ -534,23 +478,21 @@ gemm_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
                                 const unsigned long long ad =
                                     adesc0 + ((unsigned long long)((a_used + (uint32_t)(hi - i)) % NA) * (A_TILE >> 4));
                                 // four MMAs per 128-byte row: advance the start address by 32 bytes each
-                                mma_pair<KIND>(d, ad, bd, idesc, acc);
-                                mma_pair<KIND>(d, ad + 2, bd + 2, idesc, 1u);
-                                mma_pair<KIND>(d, ad + 4, bd + 4, idesc, 1u);
-                                mma_pair<KIND>(d, ad + 6, bd + 6, idesc, 1u);
+                                mma<KIND>(d, ad, bd, idesc, acc);
+                                mma<KIND>(d, ad + 2, bd + 2, idesc, 1u);
+                                mma<KIND>(d, ad + 4, bd + 4, idesc, 1u);
+                                mma<KIND>(d, ad + 6, bd + 6, idesc, 1u);
                                 acc = 1;
                                 any = true;
                             }
-                            mma_commit(bempty0 + bs * 8);
-                            mma_commit(bempty1 + bs * 8);
+                            mma_commit(&ctl->bempty[bs]);
                             ++b_used;
                             // release the A tiles no later B of this K-step needs: i > min(hi, L2 - j - 1)
                             const int L2 = L1 + nl - 1;
                             const int keep = j < hi ? (L2 - j - 1 < hi ? L2 - j - 1 : hi) : lo - 1;
                             while (a_free < hi - keep) {
                                 const uint32_t as = (a_used + (uint32_t)a_free) % NA;
-                                mma_commit(aempty0 + as * 8);
-                                mma_commit(aempty1 + as * 8);
+                                mma_commit(&ctl->aempty[as]);
                                 ++a_free;
                             }
                         }
@@ -558,33 +500,31 @@ gemm_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
                         a_used += (uint32_t)(hi - lo + 1);
                     }
                     if (!ok) break;
-                    mma_commit(tfull0 + buf * 8);
-                    mma_commit(tfull1 + buf * 8);
+                    mma_commit(&ctl->tfull[buf]);
                     ++npass;
                 } while (it.next(p));
             }
             if (ok && me == 0) {
-                // tail: both buffers' last drains (the follower's arrivals land here) are done
+                // tail: both buffers' last drains are done
                 for (uint32_t q = npass > 2 ? npass - 2 : 0; q < npass && ok; ++q)
                     ok = wait_fast(&ctl->tempty[q & 1], (q >> 1) & 1, ctl, p);
             }
             if (any) {
                 // every MMA this thread issued has completed before TMEM is released
-                mma_commit(smem_u32(&ctl->drain[me]));
+                mma_commit(&ctl->drain[me]);
                 mbar_drain_wait(&ctl->drain[me], 0, p.status);
             }
         }
     } else {
         asm volatile("setmaxnreg.inc.sync.aligned.u32 %0;" ::"n"(REG_HIGH));
         // ------------------------------------------------------------ epilogue
-        // Warp e = warp - 4 reads TMEM lanes 32 (warp % 4) .. + 31 and owns columns
+        // Warp e = warp - 8 reads TMEM lanes 32 (warp % 4) .. + 31 and owns columns
         // half * 64 .. + 63 of the tile: one output row and 64 columns per thread.
-        const int e = warp - 4;
+        const int e = warp - 8;
         const int q4 = warp & 3;
         const int row = q4 * 32 + lane;  // TMEM lane = row of this CTA's 128
         const int half = e >> 2;
         const uint32_t tl = tmem + ((uint32_t)(q4 * 32) << 16);
-        const uint32_t tempty0 = peer_addr(smem_u32(&ctl->tempty[0]), 0);
         typedef typename std::conditional<FIXED, long long, double>::type acc_t;
         acc_t sum[COLS_PER_THREAD];
         uint32_t npass = 0;
@@ -592,11 +532,11 @@ gemm_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
         // Every epilogue warp walks all items and meets every epi_sync even after an abort
         // (it then skips the waits and TMEM reads), so no warp can be left at a named
         // barrier that a warp which gave up will never reach.
-        for (int item = pair; item < p.nitems; item += npairs) {
+        for (int item = cta; item < p.nitems; item += nctas) {
             const Item w = item_of(p, item);
             if (w.skip) continue;
             // this item's output row and column tables (the previous item's writes are done)
-            const int m = w.m0 + (int)rank * BM + row;
+            const int m = w.m0 + row;
             const long long ro = (m < p.M) ? map2(p.out.rmap, m) : -1;
             const int eAr = (p.eA && m < p.M) ? p.eA[p.rowA0 + m] : 0;
             epi_sync();
@@ -627,7 +567,7 @@ gemm_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
                         // the buffer is read: hand it back to the MMA issuers
                         fence_before();
                         __syncwarp();
-                        if (lane == 0) mbar_arrive_cluster(tempty0 + buf * 8);
+                        if (lane == 0) mbar_arrive(&ctl->tempty[buf]);
                     }
                     if (FIXED) {
                         // exact int64 fixed point (2^-fixF of a level-0 unit); a level pair is combined
@@ -680,10 +620,9 @@ gemm_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
 
     fence_before();
     __syncthreads();
-    cluster_sync();  // no CTA leaves while its peer may still read its shared memory or signal it
     fence_after();
     if (warp == 1) {
-        asm volatile("tcgen05.dealloc.cta_group::2.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TMEM_COLS));
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TMEM_COLS));
     }
 }
 
@@ -724,35 +663,25 @@ cudaError_t launch(const CUtensorMap& ma, const CUtensorMap& mb, const Params& p
 {
     static std::once_flag once;
     static cudaError_t attr_err = cudaSuccess;
-    static int max_pairs = 0;
-    cudaLaunchConfig_t cfg{};
-    cfg.blockDim = dim3(THREADS);
-    cfg.dynamicSmemBytes = SMEM_BYTES;
-    cfg.stream = s;
-    cudaLaunchAttribute attr[1];
-    attr[0].id = cudaLaunchAttributeClusterDimension;
-    attr[0].val.clusterDim.x = 2;
-    attr[0].val.clusterDim.y = 1;
-    attr[0].val.clusterDim.z = 1;
-    cfg.attrs = attr;
-    cfg.numAttrs = 1;
-    std::call_once(once, [&cfg] {
+    static int max_ctas = 0;
+    std::call_once(once, [] {
         attr_err = cudaFuncSetAttribute(gemm_tc_kernel<KIND, FIXED>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                         (int)SMEM_BYTES);
-        // persistent: as many pairs as are resident on the device at once
-        int n = 0;
-        cfg.gridDim = dim3(2 * 64);
+        // persistent: as many CTAs as are resident on the device at once (one per SM)
+        int per_sm = 0;
         if (attr_err != cudaSuccess ||
-            cudaOccupancyMaxActiveClusters(&n, gemm_tc_kernel<KIND, FIXED>, &cfg) != cudaSuccess || n <= 0) {
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, gemm_tc_kernel<KIND, FIXED>, THREADS, SMEM_BYTES) !=
+                cudaSuccess ||
+            per_sm <= 0) {
             cudaGetLastError();
-            n = device_sm_count() / 2;
+            per_sm = 1;
         }
-        max_pairs = n;
+        max_ctas = per_sm * device_sm_count();
     });
     if (attr_err != cudaSuccess) return attr_err;
-    const int pairs = p.nitems < max_pairs ? p.nitems : max_pairs;
-    cfg.gridDim = dim3((unsigned)(2 * pairs));
-    return cudaLaunchKernelEx(&cfg, gemm_tc_kernel<KIND, FIXED>, ma, mb, p);
+    const int ctas = p.nitems < max_ctas ? p.nitems : max_ctas;
+    gemm_tc_kernel<KIND, FIXED><<<ctas, THREADS, SMEM_BYTES, s>>>(ma, mb, p);
+    return cudaGetLastError();
 }
 
 }  // namespace
@@ -838,7 +767,7 @@ cudaError_t gemm_tc(const GemmTc& g, cudaStream_t s)
     p.out = g.out;
     p.status = g.status;
     p.wait_ns = g.wait_ns;
-    p.tiles_m = (g.M + 2 * BM - 1) / (2 * BM);
+    p.tiles_m = (g.M + BM - 1) / BM;
     p.tiles_n = (g.N + BN - 1) / BN;
     p.group_m = p.tiles_m < 8 ? p.tiles_m : 8;
     const long long nitems = (long long)p.tiles_m * p.tiles_n * p.ksplit;
@@ -846,7 +775,7 @@ cudaError_t gemm_tc(const GemmTc& g, cudaStream_t s)
     p.nitems = (int)nitems;
     CUtensorMap ma, mb;
     if (!make_map(&ma, g.A, g.kind, g.K, g.pitchA, g.rowsA, g.slices, BM)) return cudaErrorInvalidValue;
-    if (!make_map(&mb, g.B, g.kind, g.K, g.pitchB, g.rowsB, g.slices, BNH)) return cudaErrorInvalidValue;
+    if (!make_map(&mb, g.B, g.kind, g.K, g.pitchB, g.rowsB, g.slices, BN)) return cudaErrorInvalidValue;
     cudaError_t err;
     if (g.kind == TC_BF16)
         err = fixed ? launch<TC_BF16, true>(ma, mb, p, s) : launch<TC_BF16, false>(ma, mb, p, s);

@@ -7,6 +7,8 @@
 //   CC_PROBE_TC_BF16     tcgen05.mma kind::f16 with BF16 operands, M=128 N=256 K=16 (emulated
 //                        FP64 slices and the BF16 mode)
 //   CC_PROBE_TC_TF32     tcgen05.mma kind::tf32, M=128 N=256 K=8 (the TF32 mode)
+//   CC_PROBE_IMMA        legacy INT8 tensor-core MMA (mma.sync.m16n8k32.s8), the only INT8 MMA that
+//                        assembles for sm_103a (tcgen05 has no kind::i8 there), for the record
 //
 // Each probe keeps the unit busy from registers or shared memory only (no
 // global-memory operands), times itself with CUDA events around the launch and
@@ -41,6 +43,26 @@ __global__ void __launch_bounds__(256) dmma_probe_kernel(int iters, double seed)
 #pragma unroll
     for (int q = 0; q < 8; ++q) s += d[q][0] + d[q][1];
     if (s == 1234.5678) g_probe_sink = s;
+}
+
+__global__ void __launch_bounds__(256) imma_probe_kernel(int iters, int seed)
+{
+    const int a = seed * 0x01010101 + (int)threadIdx.x, b = 0x02030405 ^ seed;
+    int d[8][4];
+#pragma unroll
+    for (int q = 0; q < 8; ++q) d[q][0] = d[q][1] = d[q][2] = d[q][3] = q;
+    for (int it = 0; it < iters; ++it) {
+#pragma unroll
+        for (int q = 0; q < 8; ++q)
+            asm volatile("mma.sync.aligned.m16n8k32.row.col.s32.s8.s8.s32 {%0,%1,%2,%3}, {%4,%4,%4,%4}, {%5,%5}, "
+                         "{%0,%1,%2,%3};"
+                         : "+r"(d[q][0]), "+r"(d[q][1]), "+r"(d[q][2]), "+r"(d[q][3])
+                         : "r"(a), "r"(b));
+    }
+    int s = 0;
+#pragma unroll
+    for (int q = 0; q < 8; ++q) s += d[q][0] + d[q][1] + d[q][2] + d[q][3];
+    if (s == 1234567) g_probe_sink = s;
 }
 
 __global__ void __launch_bounds__(256) dfma_probe_kernel(int iters, double seed)
@@ -158,8 +180,9 @@ extern "C" int cc_ladder_peak_probe(int which, int iters, void* stream, double* 
 {
     using namespace cc;
     if (!tflops) return CC_ERR_NULL;
-    if (which < CC_PROBE_DMMA || which > CC_PROBE_TC_TF32 || iters < 1 || iters > (1 << 24)) return CC_ERR_ARG;
-    if (which >= CC_PROBE_TC_BF16 && !tc_gemm_available()) return CC_ERR_UNSUPPORTED;
+    if (which < CC_PROBE_DMMA || which > CC_PROBE_IMMA || iters < 1 || iters > (1 << 24)) return CC_ERR_ARG;
+    const bool tc = which == CC_PROBE_TC_BF16 || which == CC_PROBE_TC_TF32;
+    if (tc && !tc_gemm_available()) return CC_ERR_UNSUPPORTED;
     cudaStream_t st = (cudaStream_t)stream;
     const int nsm = device_sm_count();
     cudaEvent_t e0 = nullptr, e1 = nullptr;
@@ -169,7 +192,7 @@ extern "C" int cc_ladder_peak_probe(int which, int iters, void* stream, double* 
     cudaError_t err = cudaMemcpyToSymbolAsync(g_probe_status, &zero, sizeof(int), 0, cudaMemcpyHostToDevice, st);
     // 48 KB of operand tiles, padded so that one CTA fills an SM (its tensor core and TMEM)
     const size_t tc_smem = 120 * 1024;
-    if (err == cudaSuccess && which >= CC_PROBE_TC_BF16) {
+    if (err == cudaSuccess && tc) {
         err = cudaFuncSetAttribute(tc_probe_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tc_smem);
         if (err == cudaSuccess)
             err = cudaFuncSetAttribute(tc_probe_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tc_smem);
@@ -184,6 +207,10 @@ extern "C" int cc_ladder_peak_probe(int which, int iters, void* stream, double* 
         case CC_PROBE_DFMA:
             dfma_probe_kernel<<<nsm * 8, 256, 0, st>>>(iters, 0.5);
             flops = (double)nsm * 8 * 256 * iters * 8 * 2.0;
+            break;
+        case CC_PROBE_IMMA:
+            imma_probe_kernel<<<nsm * 8, 256, 0, st>>>(iters, 3);
+            flops = (double)nsm * 8 * (256 / 32) * iters * 8 * (2.0 * 16 * 8 * 32);
             break;
         case CC_PROBE_TC_BF16:
             tc_probe_kernel<false><<<nsm, 128, tc_smem, st>>>(iters, 2000000000ull);

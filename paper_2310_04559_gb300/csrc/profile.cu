@@ -20,12 +20,12 @@ namespace {
 struct Pending {
     std::string name;
     cudaEvent_t e0, e1;
-    double flops;
+    double flops, bytes;
 };
 struct Total {
     std::string name;
     int launches;
-    double ms, flops;
+    double ms, flops, bytes;
 };
 
 std::atomic<long long> g_launches{0};
@@ -55,8 +55,12 @@ void drain_locked()
         cudaEventElapsedTime(&ms, p.e0, p.e1);
         bool found = false;
         for (auto& t : g_totals)
-            if (t.name == p.name) { t.launches += 1; t.ms += ms; t.flops += p.flops; found = true; break; }
-        if (!found) g_totals.push_back(Total{p.name, 1, ms, p.flops});
+            if (t.name == p.name) {
+                t.launches += 1; t.ms += ms; t.flops += p.flops; t.bytes += p.bytes;
+                found = true;
+                break;
+            }
+        if (!found) g_totals.push_back(Total{p.name, 1, ms, p.flops, p.bytes});
         g_pool.push_back(p.e0);
         g_pool.push_back(p.e1);
     }
@@ -67,7 +71,8 @@ void drain_locked()
 
 void count_launch(int n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
 
-ProfScope::ProfScope(const char* name, cudaStream_t s, double flops) : name_(name), s_(s), flops_(flops), e0_(nullptr)
+ProfScope::ProfScope(const char* name, cudaStream_t s, double flops, double bytes)
+    : name_(name), s_(s), flops_(flops), bytes_(bytes), e0_(nullptr)
 {
     nvtxRangePushA(name);
     if (!g_enabled.load(std::memory_order_relaxed)) return;
@@ -83,7 +88,7 @@ ProfScope::~ProfScope()
     std::lock_guard<std::mutex> lk(g_mu);
     cudaEvent_t e1 = get_event();
     cudaEventRecord(e1, s_);
-    g_pending.push_back(Pending{name_, (cudaEvent_t)e0_, e1, flops_});
+    g_pending.push_back(Pending{name_, (cudaEvent_t)e0_, e1, flops_, bytes_});
 }
 
 }  // namespace cc
@@ -110,6 +115,7 @@ int cc_ladder_profile_read(cc_ladder_profile_entry* out, int max_entries)
             out[i].launches = cc::g_totals[i].launches;
             out[i].ms = cc::g_totals[i].ms;
             out[i].flops = cc::g_totals[i].flops;
+            out[i].bytes = cc::g_totals[i].bytes;
         }
     }
     return n;

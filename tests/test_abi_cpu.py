@@ -190,7 +190,7 @@ def test_binding_refuses_cpu_tensors(lib):
 def test_probe_and_partition_argument_errors(lib):
     out = ctypes.c_double()
     assert lib.cc_ladder_peak_probe(0, 10, None, ctypes.byref(out)) == -9   # unknown probe
-    assert lib.cc_ladder_peak_probe(5, 10, None, ctypes.byref(out)) == -9
+    assert lib.cc_ladder_peak_probe(6, 10, None, ctypes.byref(out)) == -9
     assert lib.cc_ladder_peak_probe(1, 0, None, ctypes.byref(out)) == -9    # no iterations
     assert lib.cc_ladder_peak_probe(1, 10, None, None) == -2
     bounds = (ctypes.c_int * 5)()
