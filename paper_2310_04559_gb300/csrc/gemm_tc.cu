@@ -39,10 +39,14 @@
 //
 // Roles (512 threads, four warpgroups): warps 0, 3 (A slices) and 4, 5 (B slices) are TMA
 // producers, each issuing every other copy of its operand -- one thread keeps only about one
-// copy in flight per 0.3 us (measured), fewer than the tensor pipe consumes.  Warps 1-2 issue
-// the MMAs (one per level of a pass; warp 1 allocates TMEM), warps 6-7 idle, warps 8-15 are
-// the epilogue (two per TMEM lane quarter).  setmaxnreg moves registers from warpgroups 0-1 to
-// the epilogue warpgroups, which hold the running sums.
+// copy in flight per 0.3 us (measured), fewer than the tensor pipe consumes.  Warps 2 (A) and
+// 6 (B) wait for the copies to land and publish per-operand counts in shared memory; one
+// thread of warp 1 issues all MMAs and slot releases (warp 1 also allocates TMEM), reading
+// those counts instead of testing a barrier per tile -- a barrier test stalls the issuing
+// thread for about as long as two MMAs take, which with per-tile tests kept the tensor pipe
+// busy only about a third of the time (measured).  Warp 7 idles; warps 8-15 are the epilogue
+// (two per TMEM lane quarter).  setmaxnreg moves registers from warpgroups 0-1 to the
+// epilogue warpgroups, which hold the running sums.
 //
 // Every mbarrier wait is bounded (globaltimer); on expiry the CTA raises a
 // shared abort flag and the device status word, drains what it has in flight
@@ -65,17 +69,16 @@ constexpr int BN = 128;                        // output columns per tile
 constexpr int ROW_BYTES = 128;                 // K bytes per tile row: one 128-byte swizzle atom
 constexpr int A_TILE = BM * ROW_BYTES;         // 16 KB per A slice tile
 constexpr int B_TILE = BN * ROW_BYTES;         // 16 KB per B slice tile
-constexpr int NA = 6, NB = 6;                  // A FIFO and B ring slots
-constexpr int TILE_SMEM = NA * A_TILE + NB * B_TILE;  // 192 KB
+constexpr int NS = 6;                          // ring slots per operand
+constexpr int TILE_SMEM = NS * (A_TILE + B_TILE);  // 192 KB
 constexpr int MAX_SLICES = 8;
-constexpr int ISSUERS = 2;                     // MMA-issuing warps (one per level of a pass)
 constexpr int EPI_WARPS = 8;                   // two per TMEM lane quarter
 constexpr int EPI_THREADS = 32 * EPI_WARPS;
-constexpr int THREADS = 32 * 8 + EPI_THREADS;  // 512: producers and MMA issuers, then the epilogue
+constexpr int THREADS = 32 * 8 + EPI_THREADS;  // 512: producers, waiters and MMA issuer, then the epilogue
 constexpr int TMEM_COLS = 512;                 // 2 buffers x 2 levels x BN columns
 constexpr int COLS_PER_THREAD = BN / 2;        // 64 accumulator columns per epilogue thread
-// setmaxnreg split of the 512 x 128 registers of the launch: warpgroups 0-1 (producers, MMA
-// issuers) keep 64, the two epilogue warpgroups (running sums) get 192: 256 * 64 + 256 * 192 = 512 * 128.
+// setmaxnreg split of the 512 x 128 registers of the launch: warpgroups 0-1 (producers, waiters,
+// MMA issuer) keep 64, the two epilogue warpgroups (running sums) get 192: 256 * 64 + 256 * 192 = 512 * 128.
 constexpr int REG_LAUNCH = 128, REG_LOW = 64, REG_HIGH = 192;
 static_assert(256 * REG_LOW + 256 * REG_HIGH <= THREADS * REG_LAUNCH, "register split exceeds the launch's share");
 constexpr unsigned long long kDrainLimitNs = 1000000000ull;  // bound on the abort-path drains
@@ -83,10 +86,11 @@ constexpr unsigned long long kDrainLimitNs = 1000000000ull;  // bound on the abo
 enum OutKind { OUT_F64 = 0, OUT_I64 = 1, OUT_I64_RED = 2 };
 
 struct SmemCtl {
-    unsigned long long afull[NA], aempty[NA];
-    unsigned long long bfull[NB], bempty[NB];
+    unsigned long long afull[NS], bfull[NS];
+    unsigned long long empty[NS];              // slot s of both rings released
     unsigned long long tfull[2], tempty[2];
-    unsigned long long drain[ISSUERS];
+    unsigned long long drain;
+    unsigned int ready_a, ready_b;             // A / B tiles landed so far, in sequence order
     unsigned int tmem_base;
     volatile int abort;
     long long coloff[BN];                      // -1 for columns beyond N
@@ -168,6 +172,41 @@ __device__ __forceinline__ void mbar_drain_wait(unsigned long long* b, uint32_t 
     const unsigned long long t0 = gtime();
     while (!mbar_try(b, parity)) {
         if (gtime() - t0 > kDrainLimitNs) { atomicOr(status, kStatusDrainExpired); return; }
+    }
+}
+
+__device__ __forceinline__ void publish(unsigned int* ctr, unsigned int v)
+{
+    asm volatile("st.release.cta.shared::cta.u32 [%0], %1;" ::"r"(smem_u32(ctr)), "r"(v) : "memory");
+}
+
+__device__ __forceinline__ unsigned int observe(unsigned int* ctr)
+{
+    unsigned int v;
+    asm volatile("ld.acquire.cta.shared::cta.u32 %0, [%1];" : "=r"(v) : "r"(smem_u32(ctr)) : "memory");
+    return v;
+}
+
+// Tile `idx` of a sequence has landed once the published count exceeds it.  `known` caches
+// the last count read, so the common case costs one register compare; a miss spins on the
+// shared counter with the same bound and abort check as the barrier waits.
+__device__ __forceinline__ bool landed(unsigned int* ctr, uint32_t idx, uint32_t& known, SmemCtl* ctl, const Params& p)
+{
+    if ((int)(known - idx) > 0) return true;
+    known = observe(ctr);
+    if ((int)(known - idx) > 0) return true;
+    const unsigned long long t0 = gtime();
+    for (unsigned it = 1;; ++it) {
+        known = observe(ctr);
+        if ((int)(known - idx) > 0) return true;
+        if ((it & 15) == 0) {
+            if (ctl->abort) return false;
+            if (gtime() - t0 > p.wait_ns) {
+                ctl->abort = 1;
+                atomicOr(p.status, kStatusWaitExpired);
+                return false;
+            }
+        }
     }
 }
 
@@ -335,14 +374,80 @@ struct PassIter {
     }
 };
 
+// MMA issuer state carried across K-steps and passes.
+struct IssueState {
+    unsigned long long adesc0, bdesc0;  // descriptors of ring slot 0
+    uint32_t idesc, d0, fresh;          // instruction descriptor, pass buffer, levels not yet written
+    uint32_t used;                      // tiles of either operand consumed so far (the counts agree)
+    uint32_t slot0;                     // ring slot of the current K-step's first tile (= used % NS)
+    uint32_t known_a, known_b;          // last landed counts read
+};
+
+__device__ __forceinline__ uint32_t slot_add(uint32_t a, int k)  // (a + k) % NS for a < NS, k <= 2 NS
+{
+    uint32_t r = a + (uint32_t)k;
+    r = r >= (uint32_t)NS ? r - NS : r;
+    return r >= (uint32_t)NS ? r - NS : r;
+}
+
+// One K-step of a pass over levels L1 = hi - nl + 1 .. hi, slices 0 .. hi (the host admits no
+// level above slices - 1, so every pass has this shape).  B_j meets A_i for each level L of the
+// pass (i = L - j).  The A tiles arrive in order i = hi .. 0, so A tile number j (slice hi - j)
+// is last used with B_j: both tiles number j of the K-step sit in the same ring slot and leave
+// with one commit.  HI >= 0 fixes the shape at compile time (the loops unroll and the slot
+// arithmetic folds -- with the shape at run time the issuing thread, not the tensor pipe, set
+// the pace); HI < 0 takes any shape at run time.
+template <int KIND, int HI, int NL>
+__device__ __forceinline__ bool issue_kstep(IssueState& st, int hi_rt, int nl_rt, SmemCtl* ctl, const Params& p)
+{
+    const int hi = HI >= 0 ? HI : hi_rt;
+    const int nl = HI >= 0 ? NL : nl_rt;
+    const int L1 = hi - nl + 1;
+#pragma unroll
+    for (int j = 0; j <= hi; ++j) {
+        const int imin = L1 - j > 0 ? L1 - j : 0;  // lowest A slice that B_j meets
+        if (!landed(&ctl->ready_a, st.used + (uint32_t)(hi - imin), st.known_a, ctl, p) ||
+            !landed(&ctl->ready_b, st.used + (uint32_t)j, st.known_b, ctl, p))
+            return false;
+        fence_after();
+        const uint32_t bs = slot_add(st.slot0, j);
+        const unsigned long long bd = st.bdesc0 + (unsigned long long)bs * (B_TILE >> 4);
+#pragma unroll
+        for (int lv = 0; lv < nl; ++lv) {
+            const int i = L1 + lv - j;
+            if (i < 0 || i > hi) continue;
+            const unsigned long long ad = st.adesc0 + (unsigned long long)slot_add(st.slot0, hi - i) * (A_TILE >> 4);
+            const uint32_t d = st.d0 + (uint32_t)(lv * BN);
+            // four MMAs per 128-byte row: advance the start address by 32 bytes each
+            mma<KIND>(d, ad, bd, st.idesc, ((st.fresh >> lv) & 1u) ^ 1u);
+            mma<KIND>(d, ad + 2, bd + 2, st.idesc, 1u);
+            mma<KIND>(d, ad + 4, bd + 4, st.idesc, 1u);
+            mma<KIND>(d, ad + 6, bd + 6, st.idesc, 1u);
+            st.fresh &= ~(1u << lv);
+        }
+        mma_commit(&ctl->empty[bs]);
+    }
+    st.used += (uint32_t)(hi + 1);
+    st.slot0 = slot_add(st.slot0, hi + 1);
+    return true;
+}
+
+template <int KIND, int HI, int NL>
+__device__ __forceinline__ bool issue_pass(IssueState& st, int nk, int hi, int nl, SmemCtl* ctl, const Params& p)
+{
+    for (int k = 0; k < nk; ++k)
+        if (!issue_kstep<KIND, HI, NL>(st, hi, nl, ctl, p)) return false;
+    return true;
+}
+
 template <int KIND, bool FIXED>
 __global__ void __launch_bounds__(THREADS, 1)
 gemm_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, const Params p)
 {
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     unsigned char* base = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
-    unsigned char* aring = base;                      // NA x A_TILE
-    unsigned char* bring = base + NA * A_TILE;        // NB x B_TILE
+    unsigned char* aring = base;                      // NS x A_TILE
+    unsigned char* bring = base + NS * A_TILE;        // NS x B_TILE
     SmemCtl* ctl = (SmemCtl*)(base + TILE_SMEM);
 
     constexpr int KSTEP = KIND == TC_BF16 ? 64 : 32;  // K elements per 128-byte row
@@ -350,10 +455,15 @@ gemm_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
     const int cta = (int)blockIdx.x, nctas = (int)gridDim.x;
 
     if (threadIdx.x == 0) {
-        for (int s = 0; s < NA; ++s) { mbar_init(&ctl->afull[s], 1); mbar_init(&ctl->aempty[s], ISSUERS); }
-        for (int s = 0; s < NB; ++s) { mbar_init(&ctl->bfull[s], 1); mbar_init(&ctl->bempty[s], ISSUERS); }
-        for (int b = 0; b < 2; ++b) { mbar_init(&ctl->tfull[b], ISSUERS); mbar_init(&ctl->tempty[b], EPI_WARPS); }
-        for (int q = 0; q < ISSUERS; ++q) mbar_init(&ctl->drain[q], 1);
+        for (int s = 0; s < NS; ++s) {
+            mbar_init(&ctl->afull[s], 1);
+            mbar_init(&ctl->bfull[s], 1);
+            mbar_init(&ctl->empty[s], 1);
+        }
+        for (int b = 0; b < 2; ++b) { mbar_init(&ctl->tfull[b], 1); mbar_init(&ctl->tempty[b], EPI_WARPS); }
+        mbar_init(&ctl->drain, 1);
+        ctl->ready_a = 0;
+        ctl->ready_b = 0;
         ctl->abort = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
@@ -381,11 +491,10 @@ gemm_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
             const long long mine = prod & 1;
             const CUtensorMap* map = isA ? &tmA : &tmB;
             asm volatile("prefetch.tensormap [%0];" ::"l"((unsigned long long)map) : "memory");
-            const int NS = isA ? NA : NB;
             const uint32_t tile = isA ? A_TILE : B_TILE;
             unsigned char* ring = isA ? aring : bring;
             unsigned long long* full = isA ? ctl->afull : ctl->bfull;
-            unsigned long long* empty = isA ? ctl->aempty : ctl->bempty;
+            unsigned long long* empty = ctl->empty;
             long long issued = 0;  // copies of this operand in the sequence so far (all producers')
             bool ok = true;
             auto load = [&](int kb, int row, int slice) -> bool {
@@ -429,18 +538,49 @@ gemm_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
                 for (long long u = issued - 1; u >= 0 && u >= issued - NS; --u)
                     if ((u & 1) == mine) mbar_drain_wait(&full[u % NS], (uint32_t)((u / NS) & 1), p.status);
             }
-        } else if ((warp == 1 || warp == 2) && lane == 0) {
+        } else if ((warp == 2 || warp == 6) && lane == 0) {
+            // ------------------------------------------------------------ waiters
+            // One thread per operand waits for that operand's tiles in sequence order and
+            // publishes how many have landed.  The MMA issuer then reads one shared counter
+            // instead of testing a barrier per tile: a barrier test blocks the issuing thread
+            // for about 70 ns, as long as two of its MMAs take, and per-tile tests left the
+            // tensor pipe idle most of the time.
+            const bool isA = warp == 2;
+            unsigned long long* full = isA ? ctl->afull : ctl->bfull;
+            unsigned int* ctr = isA ? &ctl->ready_a : &ctl->ready_b;
+            uint32_t total = 0;  // this CTA's tiles of the operand (the same count for A and B)
+            for (int item = cta; item < p.nitems; item += nctas) {
+                const Item w = item_of(p, item);
+                if (w.skip) continue;
+                PassIter it;
+                it.begin(p, w.split);
+                do {
+                    int lo, hi;
+                    it.ranges(p, lo, hi);
+                    total += (uint32_t)((it.k1 - it.k0 + KSTEP - 1) / KSTEP) * (uint32_t)(hi - lo + 1);
+                } while (it.next(p));
+            }
+            for (uint32_t u = 0; u < total; ++u) {
+                if (!wait_fast(&full[u % NS], (u / NS) & 1, ctl, p)) break;
+                publish(ctr, u + 1);
+            }
+        } else if (warp == 1 && lane == 0) {
             // ------------------------------------------------------------ MMA
-            // Issuer `me` owns level L1 + me of a two-level pass (columns me * BN of the
-            // pass's buffer); in a one-level pass issuer 0 does all MMAs and issuer 1 only
-            // paces, releases and commits.  Both walk the same tile sequence, wait for the
-            // same tiles and release every slot (arrival count 2 each).
-            const int me = warp - 1;
-            const uint32_t idesc = instr_desc<KIND>();
+            // One issuing thread for both levels of a pass (accumulator columns lv * BN of the
+            // pass's buffer).  It walks the producers' tile sequence, learns from the waiters'
+            // counters which tiles have landed, and releases every slot with a commit once the
+            // MMAs that read it are done.
+            IssueState st;
+            st.idesc = instr_desc<KIND>();
             // slot q's descriptor = slot 0's + q * tile_bytes / 16 in the start-address field
             // (shared addresses stay below 256 KB, so the 14-bit field never carries over)
-            const unsigned long long adesc0 = smem_desc(aring), bdesc0 = smem_desc(bring);
-            uint32_t a_used = 0, b_used = 0, npass = 0;
+            st.adesc0 = smem_desc(aring);
+            st.bdesc0 = smem_desc(bring);
+            st.used = 0;
+            st.slot0 = 0;
+            st.known_a = 0;
+            st.known_b = 0;
+            uint32_t npass = 0;
             bool ok = true, any = false;
             for (int item = cta; item < p.nitems && ok; item += nctas) {
                 const Item w = item_of(p, item);
@@ -449,70 +589,38 @@ gemm_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
                 it.begin(p, w.split);
                 do {
                     int lo, hi;
-                    it.ranges(p, lo, hi);
-                    const int L1 = p.glo[it.g], nl = p.gn[it.g];
-                    const bool active = me < nl;
-                    const int mylevel = L1 + me;
+                    it.ranges(p, lo, hi);  // lo = 0 and hi = the pass's top level
+                    const int nl = p.gn[it.g];
                     const int buf = (int)(npass & 1);
                     const uint32_t use = npass >> 1;  // earlier passes on this buffer
                     if (!wait_fast(&ctl->tempty[buf], (use & 1) ^ 1, ctl, p)) { ok = false; break; }
                     fence_after();
-                    const uint32_t d = tmem + (uint32_t)(buf * 2 * BN + me * BN);
-                    uint32_t acc = 0;
-                    for (int kb = it.k0; kb < it.k1 && ok; kb += KSTEP) {
-                        int a_wait = 0, a_free = 0;  // A tiles of this K-step waited for / released
-                        for (int j = lo; j <= hi; ++j) {
-                            const int imin = L1 - j > lo ? L1 - j : lo;
-                            while (a_wait < hi - imin + 1) {
-                                const uint32_t u = a_used + (uint32_t)a_wait;
-                                if (!wait_fast(&ctl->afull[u % NA], (u / NA) & 1, ctl, p)) { ok = false; break; }
-                                ++a_wait;
-                            }
-                            if (!ok) break;
-                            const uint32_t bs = b_used % NB;
-                            if (!wait_fast(&ctl->bfull[bs], (b_used / NB) & 1, ctl, p)) { ok = false; break; }
-                            fence_after();
-                            const int i = mylevel - j;
-                            if (active && i >= lo && i <= hi) {
-                                const unsigned long long bd = bdesc0 + ((unsigned long long)bs * (B_TILE >> 4));
-                                const unsigned long long ad =
-                                    adesc0 + ((unsigned long long)((a_used + (uint32_t)(hi - i)) % NA) * (A_TILE >> 4));
-                                // four MMAs per 128-byte row: advance the start address by 32 bytes each
-                                mma<KIND>(d, ad, bd, idesc, acc);
-                                mma<KIND>(d, ad + 2, bd + 2, idesc, 1u);
-                                mma<KIND>(d, ad + 4, bd + 4, idesc, 1u);
-                                mma<KIND>(d, ad + 6, bd + 6, idesc, 1u);
-                                acc = 1;
-                                any = true;
-                            }
-                            mma_commit(&ctl->bempty[bs]);
-                            ++b_used;
-                            // release the A tiles no later B of this K-step needs: i > min(hi, L2 - j - 1)
-                            const int L2 = L1 + nl - 1;
-                            const int keep = j < hi ? (L2 - j - 1 < hi ? L2 - j - 1 : hi) : lo - 1;
-                            while (a_free < hi - keep) {
-                                const uint32_t as = (a_used + (uint32_t)a_free) % NA;
-                                mma_commit(&ctl->aempty[as]);
-                                ++a_free;
-                            }
-                        }
-                        if (!ok) break;
-                        a_used += (uint32_t)(hi - lo + 1);
+                    st.d0 = tmem + (uint32_t)(buf * 2 * BN);
+                    st.fresh = (1u << nl) - 1;
+                    const int nk = (it.k1 - it.k0 + KSTEP - 1) / KSTEP;
+                    switch (hi * 4 + nl) {  // the shapes the host builds for up to 8 slices
+                        case 0 * 4 + 1: ok = issue_pass<KIND, 0, 1>(st, nk, hi, nl, ctl, p); break;
+                        case 1 * 4 + 2: ok = issue_pass<KIND, 1, 2>(st, nk, hi, nl, ctl, p); break;
+                        case 3 * 4 + 2: ok = issue_pass<KIND, 3, 2>(st, nk, hi, nl, ctl, p); break;
+                        case 5 * 4 + 2: ok = issue_pass<KIND, 5, 2>(st, nk, hi, nl, ctl, p); break;
+                        case 7 * 4 + 2: ok = issue_pass<KIND, 7, 2>(st, nk, hi, nl, ctl, p); break;
+                        default: ok = issue_pass<KIND, -1, 0>(st, nk, hi, nl, ctl, p); break;
                     }
                     if (!ok) break;
+                    any = true;
                     mma_commit(&ctl->tfull[buf]);
                     ++npass;
                 } while (it.next(p));
             }
-            if (ok && me == 0) {
+            if (ok) {
                 // tail: both buffers' last drains are done
                 for (uint32_t q = npass > 2 ? npass - 2 : 0; q < npass && ok; ++q)
                     ok = wait_fast(&ctl->tempty[q & 1], (q >> 1) & 1, ctl, p);
             }
             if (any) {
                 // every MMA this thread issued has completed before TMEM is released
-                mma_commit(&ctl->drain[me]);
-                mbar_drain_wait(&ctl->drain[me], 0, p.status);
+                mma_commit(&ctl->drain);
+                mbar_drain_wait(&ctl->drain, 0, p.status);
             }
         }
     } else {
@@ -564,7 +672,7 @@ gemm_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
                     if (nl == 2) tmem_ld8(tb + (uint32_t)(BN + cc * 8), r1);
                     tmem_wait_ld();
                     if (cc == COLS_PER_THREAD / 8 - 1) {
-                        // the buffer is read: hand it back to the MMA issuers
+                        // the buffer is read: hand it back to the MMA issuer
                         fence_before();
                         __syncwarp();
                         if (lane == 0) mbar_arrive(&ctl->tempty[buf]);
@@ -749,7 +857,8 @@ cudaError_t gemm_tc(const GemmTc& g, cudaStream_t s)
     p.scale_base = g.scale_base; p.beta = g.beta; p.nslices = g.slices;
     p.ngroups = g.ngroups;
     for (int i = 0; i < g.ngroups; ++i) {
-        if (g.gn[i] < 1 || g.gn[i] > 2 || g.glo[i] < 0 || g.glo[i] + g.gn[i] - 1 > 2 * (g.slices - 1))
+        // levels up to slices - 1 only: every pass then has the shape the MMA issuer assumes
+        if (g.gn[i] < 1 || g.gn[i] > 2 || g.glo[i] < 0 || g.glo[i] + g.gn[i] - 1 > g.slices - 1)
             return cudaErrorInvalidValue;
         if (g.gkc[i] < 0 || g.gkc[i] % kstep) return cudaErrorInvalidValue;
         if (!fixed && g.gn[i] != 1) return cudaErrorInvalidValue;  // FP64 sums take one level per pass
@@ -761,6 +870,7 @@ cudaError_t gemm_tc(const GemmTc& g, cudaStream_t s)
     p.ksplit = g.ksplit > 1 ? g.ksplit : 1;
     if (p.ksplit > 1 && g.epi != EPI_FIXED64_ADD) return cudaErrorInvalidValue;
     p.kper = (int)((((long long)g.K + p.ksplit - 1) / p.ksplit + kstep - 1) / kstep * kstep);
+    if ((long long)p.kper * (p.ksplit - 1) >= g.K) return cudaErrorInvalidValue;  // every split owns some K
     if ((g.tri_rdiv > 0) != (g.tri_cdiv > 0) || g.tri_rdiv < 0) return cudaErrorInvalidValue;
     p.tri_rdiv = g.tri_rdiv;
     p.tri_cdiv = g.tri_cdiv;
