@@ -37,14 +37,14 @@
 // i = hi..lo through a FIFO, so B_j meets every A_i with i + j in the pass while
 // A_i lives only until its last partner has passed.
 //
-// Roles (512 threads, four warpgroups): warps 0, 3 (A slices) and 4, 5 (B slices) are TMA
+// Roles (512 threads, four warpgroups): warps 0, 4 (A slices) and 3, 7 (B slices) are TMA
 // producers, each issuing every other copy of its operand -- one thread keeps only about one
-// copy in flight per 0.3 us (measured), fewer than the tensor pipe consumes.  Warps 2 (A) and
-// 6 (B) wait for the copies to land and publish per-operand counts in shared memory; one
-// thread of warp 1 issues all MMAs and slot releases (warp 1 also allocates TMEM), reading
+// copy in flight per 0.3 us (measured), fewer than the tensor pipe consumes.  Warps 1 (A) and
+// 5 (B) wait for the copies to land and publish per-operand counts in shared memory; one
+// thread of warp 2 issues all MMAs and slot releases (warp 2 also allocates TMEM), reading
 // those counts instead of testing a barrier per tile -- a barrier test stalls the issuing
 // thread for about as long as two MMAs take, which with per-tile tests kept the tensor pipe
-// busy only about a third of the time (measured).  Warp 7 idles; warps 8-15 are the epilogue
+// busy only about a third of the time (measured).  Warp 6 idles; warps 8-15 are the epilogue
 // (two per TMEM lane quarter).  setmaxnreg moves registers from warpgroups 0-1 to the
 // epilogue warpgroups, which hold the running sums.
 //
@@ -80,6 +80,10 @@ constexpr int COLS_PER_THREAD = BN / 2;        // 64 accumulator columns per epi
 // setmaxnreg split of the 512 x 128 registers of the launch: warpgroups 0-1 (producers, waiters,
 // MMA issuer) keep 64, the two epilogue warpgroups (running sums) get 192: 256 * 64 + 256 * 192 = 512 * 128.
 constexpr int REG_LAUNCH = 128, REG_LOW = 64, REG_HIGH = 192;
+// Warp roles.  A warp runs on SM sub-partition warp % 4: the MMA issuer (warp 2) shares its
+// sub-partition only with the idle warp 6 and two epilogue warps, not with a producer or a
+// waiter (that measured 3-4% faster).  Producers: warps 0, 4 (A slices) and 3, 7 (B slices).
+constexpr int WARP_WAIT_A = 1, WARP_WAIT_B = 5, WARP_MMA = 2;
 static_assert(256 * REG_LOW + 256 * REG_HIGH <= THREADS * REG_LAUNCH, "register split exceeds the launch's share");
 constexpr unsigned long long kDrainLimitNs = 1000000000ull;  // bound on the abort-path drains
 
@@ -467,7 +471,7 @@ gemm_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
         ctl->abort = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
-    if (warp == 1) {
+    if (warp == WARP_MMA) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&ctl->tmem_base)),
                      "r"(TMEM_COLS));
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
@@ -479,7 +483,7 @@ gemm_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
 
     if (warp < 8) {
         asm volatile("setmaxnreg.dec.sync.aligned.u32 %0;" ::"n"(REG_LOW));
-        const int prod = warp == 0 ? 0 : warp == 3 ? 1 : warp == 4 ? 2 : warp == 5 ? 3 : -1;
+        const int prod = warp == 0 ? 0 : warp == 4 ? 1 : warp == 3 ? 2 : warp == 7 ? 3 : -1;
         if (prod >= 0 && lane == 0) {
             // -------------------------------------------------------- producers
             // Four producer threads (warps 0, 3: A slices; 4, 5: B slices), each issuing every
@@ -538,14 +542,14 @@ gemm_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
                 for (long long u = issued - 1; u >= 0 && u >= issued - NS; --u)
                     if ((u & 1) == mine) mbar_drain_wait(&full[u % NS], (uint32_t)((u / NS) & 1), p.status);
             }
-        } else if ((warp == 2 || warp == 6) && lane == 0) {
+        } else if ((warp == WARP_WAIT_A || warp == WARP_WAIT_B) && lane == 0) {
             // ------------------------------------------------------------ waiters
             // One thread per operand waits for that operand's tiles in sequence order and
             // publishes how many have landed.  The MMA issuer then reads one shared counter
             // instead of testing a barrier per tile: a barrier test blocks the issuing thread
             // for about 70 ns, as long as two of its MMAs take, and per-tile tests left the
             // tensor pipe idle most of the time.
-            const bool isA = warp == 2;
+            const bool isA = warp == WARP_WAIT_A;
             unsigned long long* full = isA ? ctl->afull : ctl->bfull;
             unsigned int* ctr = isA ? &ctl->ready_a : &ctl->ready_b;
             uint32_t total = 0;  // this CTA's tiles of the operand (the same count for A and B)
@@ -564,7 +568,7 @@ gemm_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
                 if (!wait_fast(&full[u % NS], (u / NS) & 1, ctl, p)) break;
                 publish(ctr, u + 1);
             }
-        } else if (warp == 1 && lane == 0) {
+        } else if (warp == WARP_MMA && lane == 0) {
             // ------------------------------------------------------------ MMA
             // One issuing thread for both levels of a pass (accumulator columns lv * BN of the
             // pass's buffer).  It walks the producers' tile sequence, learns from the waiters'
@@ -729,7 +733,7 @@ gemm_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
     fence_before();
     __syncthreads();
     fence_after();
-    if (warp == 1) {
+    if (warp == WARP_MMA) {
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TMEM_COLS));
     }
 }
