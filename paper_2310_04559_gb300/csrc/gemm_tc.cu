@@ -86,6 +86,8 @@ constexpr int REG_LAUNCH = 128, REG_LOW = 64, REG_HIGH = 192;
 constexpr int WARP_WAIT_A = 1, WARP_WAIT_B = 5, WARP_MMA = 2;
 static_assert(256 * REG_LOW + 256 * REG_HIGH <= THREADS * REG_LAUNCH, "register split exceeds the launch's share");
 constexpr unsigned long long kDrainLimitNs = 1000000000ull;  // bound on the abort-path drains
+// Items of at most this much K use the combined landed count (see the waiters)
+constexpr int kCombinedMaxK = 4096;
 
 enum OutKind { OUT_F64 = 0, OUT_I64 = 1, OUT_I64_RED = 2 };
 
@@ -94,7 +96,9 @@ struct SmemCtl {
     unsigned long long empty[NS];              // slot s of both rings released
     unsigned long long tfull[2], tempty[2];
     unsigned long long drain;
-    unsigned int ready_a, ready_b;             // A / B tiles landed so far, in sequence order
+    unsigned int ready_a;                      // A tiles landed, in sequence order
+    unsigned int ready_braw;                   // B tiles landed, in sequence order
+    unsigned int ready_b;                      // B tiles landed with every A tile they meet
     unsigned int tmem_base;
     volatile int abort;
     long long coloff[BN];                      // -1 for columns beyond N
@@ -114,6 +118,7 @@ struct Params {
     int ksplit, kper;              // K split: item split s owns [s*kper, min(K, (s+1)*kper))
     long long tri_rdiv, tri_cdiv;  // triangular tile skip (0 = off)
     int tiles_m, tiles_n, group_m, nitems;
+    int combined;                  // host's choice of the kernel variant: combined landed count or both raw
     OutDesc out;
     int* status;
     unsigned long long wait_ns;
@@ -194,6 +199,7 @@ __device__ __forceinline__ unsigned int observe(unsigned int* ctr)
 // Tile `idx` of a sequence has landed once the published count exceeds it.  `known` caches
 // the last count read, so the common case costs one register compare; a miss spins on the
 // shared counter with the same bound and abort check as the barrier waits.
+template <bool BACKOFF = false>
 __device__ __forceinline__ bool landed(unsigned int* ctr, uint32_t idx, uint32_t& known, SmemCtl* ctl, const Params& p)
 {
     if ((int)(known - idx) > 0) return true;
@@ -201,6 +207,7 @@ __device__ __forceinline__ bool landed(unsigned int* ctr, uint32_t idx, uint32_t
     if ((int)(known - idx) > 0) return true;
     const unsigned long long t0 = gtime();
     for (unsigned it = 1;; ++it) {
+        if (BACKOFF) __nanosleep(32);  // a waiter's spin yields issue slots to its sub-partition
         known = observe(ctr);
         if ((int)(known - idx) > 0) return true;
         if ((it & 15) == 0) {
@@ -384,7 +391,7 @@ struct IssueState {
     uint32_t idesc, d0, fresh;          // instruction descriptor, pass buffer, levels not yet written
     uint32_t used;                      // tiles of either operand consumed so far (the counts agree)
     uint32_t slot0;                     // ring slot of the current K-step's first tile (= used % NS)
-    uint32_t known_a, known_b;          // last landed counts read
+    uint32_t known_a, known_braw, known_b;  // last landed counts read
 };
 
 __device__ __forceinline__ uint32_t slot_add(uint32_t a, int k)  // (a + k) % NS for a < NS, k <= 2 NS
@@ -401,7 +408,7 @@ __device__ __forceinline__ uint32_t slot_add(uint32_t a, int k)  // (a + k) % NS
 // with one commit.  HI >= 0 fixes the shape at compile time (the loops unroll and the slot
 // arithmetic folds -- with the shape at run time the issuing thread, not the tensor pipe, set
 // the pace); HI < 0 takes any shape at run time.
-template <int KIND, int HI, int NL>
+template <int KIND, int HI, int NL, bool COMB>
 __device__ __forceinline__ bool issue_kstep(IssueState& st, int hi_rt, int nl_rt, SmemCtl* ctl, const Params& p)
 {
     const int hi = HI >= 0 ? HI : hi_rt;
@@ -409,11 +416,26 @@ __device__ __forceinline__ bool issue_kstep(IssueState& st, int hi_rt, int nl_rt
     const int L1 = hi - nl + 1;
 #pragma unroll
     for (int j = 0; j <= hi; ++j) {
+        const uint32_t idx = st.used + (uint32_t)j;
         const int imin = L1 - j > 0 ? L1 - j : 0;  // lowest A slice that B_j meets
-        if (!landed(&ctl->ready_a, st.used + (uint32_t)(hi - imin), st.known_a, ctl, p) ||
-            !landed(&ctl->ready_b, st.used + (uint32_t)j, st.known_b, ctl, p))
-            return false;
-        fence_after();
+        if (COMB) {
+            if ((int)(st.known_b - idx) <= 0) {
+                st.known_b = observe(&ctl->ready_b);
+                if ((int)(st.known_b - idx) <= 0) {
+                    // late tiles: watch the two raw counts, not the combined one, which would add
+                    // the second waiter's reaction to every late A tile
+                    if (!landed(&ctl->ready_a, st.used + (uint32_t)(hi - imin), st.known_a, ctl, p) ||
+                        !landed(&ctl->ready_braw, idx, st.known_braw, ctl, p))
+                        return false;
+                }
+                fence_after();
+            }
+        } else {
+            if (!landed(&ctl->ready_a, st.used + (uint32_t)(hi - imin), st.known_a, ctl, p) ||
+                !landed(&ctl->ready_braw, idx, st.known_braw, ctl, p))
+                return false;
+            fence_after();
+        }
         const uint32_t bs = slot_add(st.slot0, j);
         const unsigned long long bd = st.bdesc0 + (unsigned long long)bs * (B_TILE >> 4);
 #pragma unroll
@@ -436,15 +458,15 @@ __device__ __forceinline__ bool issue_kstep(IssueState& st, int hi_rt, int nl_rt
     return true;
 }
 
-template <int KIND, int HI, int NL>
+template <int KIND, int HI, int NL, bool COMB>
 __device__ __forceinline__ bool issue_pass(IssueState& st, int nk, int hi, int nl, SmemCtl* ctl, const Params& p)
 {
     for (int k = 0; k < nk; ++k)
-        if (!issue_kstep<KIND, HI, NL>(st, hi, nl, ctl, p)) return false;
+        if (!issue_kstep<KIND, HI, NL, COMB>(st, hi, nl, ctl, p)) return false;
     return true;
 }
 
-template <int KIND, bool FIXED>
+template <int KIND, bool FIXED, bool COMB>
 __global__ void __launch_bounds__(THREADS, 1)
 gemm_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, const Params p)
 {
@@ -468,6 +490,7 @@ gemm_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
         mbar_init(&ctl->drain, 1);
         ctl->ready_a = 0;
         ctl->ready_b = 0;
+        ctl->ready_braw = 0;
         ctl->abort = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
@@ -542,17 +565,14 @@ gemm_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
                 for (long long u = issued - 1; u >= 0 && u >= issued - NS; --u)
                     if ((u & 1) == mine) mbar_drain_wait(&full[u % NS], (uint32_t)((u / NS) & 1), p.status);
             }
-        } else if ((warp == WARP_WAIT_A || warp == WARP_WAIT_B) && lane == 0) {
+        } else if (warp == WARP_WAIT_A && lane == 0) {
             // ------------------------------------------------------------ waiters
-            // One thread per operand waits for that operand's tiles in sequence order and
-            // publishes how many have landed.  The MMA issuer then reads one shared counter
-            // instead of testing a barrier per tile: a barrier test blocks the issuing thread
-            // for about 70 ns, as long as two of its MMAs take, and per-tile tests left the
-            // tensor pipe idle most of the time.
-            const bool isA = warp == WARP_WAIT_A;
-            unsigned long long* full = isA ? ctl->afull : ctl->bfull;
-            unsigned int* ctr = isA ? &ctl->ready_a : &ctl->ready_b;
-            uint32_t total = 0;  // this CTA's tiles of the operand (the same count for A and B)
+            // Two threads wait for the copies to land and publish counts in shared memory; the
+            // MMA issuer then compares one shared count per B tile instead of testing barriers:
+            // a barrier test blocks the issuing thread for about 70 ns, as long as two of its
+            // MMAs take, and per-tile tests left the tensor pipe idle most of the time.  This one
+            // counts the A tiles landed, in sequence order.
+            uint32_t total = 0;  // this CTA's A tiles (as many as its B tiles)
             for (int item = cta; item < p.nitems; item += nctas) {
                 const Item w = item_of(p, item);
                 if (w.skip) continue;
@@ -565,8 +585,40 @@ gemm_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
                 } while (it.next(p));
             }
             for (uint32_t u = 0; u < total; ++u) {
-                if (!wait_fast(&full[u % NS], (u / NS) & 1, ctl, p)) break;
-                publish(ctr, u + 1);
+                if (!wait_fast(&ctl->afull[u % NS], (u / NS) & 1, ctl, p)) break;
+                publish(&ctl->ready_a, u + 1);
+            }
+        } else if (warp == WARP_WAIT_B && lane == 0) {
+            // The other counts the B tiles that have landed (raw) and, when the launch asks for
+            // it, those that have landed together with every A tile they meet (the A count is
+            // the first thread's).  With the combined count the issuer makes one compare per B
+            // tile and reads the raw counts only when tiles are late: that pays where the issue
+            // loop sets the pace (short K per item, operands from L2: +10%), and costs where the
+            // copies do (long K streamed from HBM: -15%, measured), so the host chooses.
+            uint32_t nb = 0, a_done = 0, known_a = 0;  // B tiles published, A tiles of past K-steps
+            bool ok = true;
+            for (int item = cta; item < p.nitems && ok; item += nctas) {
+                const Item w = item_of(p, item);
+                if (w.skip) continue;
+                PassIter it;
+                it.begin(p, w.split);
+                do {
+                    int lo, hi;
+                    it.ranges(p, lo, hi);
+                    const int L1 = p.glo[it.g];
+                    for (int kb = it.k0; kb < it.k1 && ok; kb += KSTEP) {
+                        for (int j = lo; j <= hi && ok; ++j) {
+                            const int imin = L1 - j > lo ? L1 - j : lo;  // lowest A slice B_j meets
+                            ok = wait_fast(&ctl->bfull[nb % NS], (nb / NS) & 1, ctl, p);
+                            if (ok) publish(&ctl->ready_braw, nb + 1);
+                            if (COMB)
+                                ok = ok && landed<true>(&ctl->ready_a, a_done + (uint32_t)(hi - imin), known_a, ctl, p);
+                            if (ok && COMB) publish(&ctl->ready_b, nb + 1);
+                            ++nb;
+                        }
+                        a_done += (uint32_t)(hi - lo + 1);
+                    }
+                } while (ok && it.next(p));
             }
         } else if (warp == WARP_MMA && lane == 0) {
             // ------------------------------------------------------------ MMA
@@ -583,6 +635,7 @@ gemm_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
             st.used = 0;
             st.slot0 = 0;
             st.known_a = 0;
+            st.known_braw = 0;
             st.known_b = 0;
             uint32_t npass = 0;
             bool ok = true, any = false;
@@ -603,12 +656,12 @@ gemm_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
                     st.fresh = (1u << nl) - 1;
                     const int nk = (it.k1 - it.k0 + KSTEP - 1) / KSTEP;
                     switch (hi * 4 + nl) {  // the shapes the host builds for up to 8 slices
-                        case 0 * 4 + 1: ok = issue_pass<KIND, 0, 1>(st, nk, hi, nl, ctl, p); break;
-                        case 1 * 4 + 2: ok = issue_pass<KIND, 1, 2>(st, nk, hi, nl, ctl, p); break;
-                        case 3 * 4 + 2: ok = issue_pass<KIND, 3, 2>(st, nk, hi, nl, ctl, p); break;
-                        case 5 * 4 + 2: ok = issue_pass<KIND, 5, 2>(st, nk, hi, nl, ctl, p); break;
-                        case 7 * 4 + 2: ok = issue_pass<KIND, 7, 2>(st, nk, hi, nl, ctl, p); break;
-                        default: ok = issue_pass<KIND, -1, 0>(st, nk, hi, nl, ctl, p); break;
+                        case 0 * 4 + 1: ok = issue_pass<KIND, 0, 1, COMB>(st, nk, hi, nl, ctl, p); break;
+                        case 1 * 4 + 2: ok = issue_pass<KIND, 1, 2, COMB>(st, nk, hi, nl, ctl, p); break;
+                        case 3 * 4 + 2: ok = issue_pass<KIND, 3, 2, COMB>(st, nk, hi, nl, ctl, p); break;
+                        case 5 * 4 + 2: ok = issue_pass<KIND, 5, 2, COMB>(st, nk, hi, nl, ctl, p); break;
+                        case 7 * 4 + 2: ok = issue_pass<KIND, 7, 2, COMB>(st, nk, hi, nl, ctl, p); break;
+                        default: ok = issue_pass<KIND, -1, 0, COMB>(st, nk, hi, nl, ctl, p); break;
                     }
                     if (!ok) break;
                     any = true;
@@ -770,19 +823,19 @@ bool make_map(CUtensorMap* m, const void* base, int kind, long long K, long long
     return r == CUDA_SUCCESS;
 }
 
-template <int KIND, bool FIXED>
+template <int KIND, bool FIXED, bool COMB>
 cudaError_t launch(const CUtensorMap& ma, const CUtensorMap& mb, const Params& p, cudaStream_t s)
 {
     static std::once_flag once;
     static cudaError_t attr_err = cudaSuccess;
     static int max_ctas = 0;
     std::call_once(once, [] {
-        attr_err = cudaFuncSetAttribute(gemm_tc_kernel<KIND, FIXED>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+        attr_err = cudaFuncSetAttribute(gemm_tc_kernel<KIND, FIXED, COMB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                         (int)SMEM_BYTES);
         // persistent: as many CTAs as are resident on the device at once (one per SM)
         int per_sm = 0;
         if (attr_err != cudaSuccess ||
-            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, gemm_tc_kernel<KIND, FIXED>, THREADS, SMEM_BYTES) !=
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, gemm_tc_kernel<KIND, FIXED, COMB>, THREADS, SMEM_BYTES) !=
                 cudaSuccess ||
             per_sm <= 0) {
             cudaGetLastError();
@@ -792,7 +845,7 @@ cudaError_t launch(const CUtensorMap& ma, const CUtensorMap& mb, const Params& p
     });
     if (attr_err != cudaSuccess) return attr_err;
     const int ctas = p.nitems < max_ctas ? p.nitems : max_ctas;
-    gemm_tc_kernel<KIND, FIXED><<<ctas, THREADS, SMEM_BYTES, s>>>(ma, mb, p);
+    gemm_tc_kernel<KIND, FIXED, COMB><<<ctas, THREADS, SMEM_BYTES, s>>>(ma, mb, p);
     return cudaGetLastError();
 }
 
@@ -884,6 +937,7 @@ cudaError_t gemm_tc(const GemmTc& g, cudaStream_t s)
     p.tiles_m = (g.M + BM - 1) / BM;
     p.tiles_n = (g.N + BN - 1) / BN;
     p.group_m = p.tiles_m < 8 ? p.tiles_m : 8;
+    p.combined = p.kper <= kCombinedMaxK ? 1 : 0;
     const long long nitems = (long long)p.tiles_m * p.tiles_n * p.ksplit;
     if (nitems > 0x7fffffffll) return cudaErrorInvalidConfiguration;
     p.nitems = (int)nitems;
@@ -892,9 +946,11 @@ cudaError_t gemm_tc(const GemmTc& g, cudaStream_t s)
     if (!make_map(&mb, g.B, g.kind, g.K, g.pitchB, g.rowsB, g.slices, BN)) return cudaErrorInvalidValue;
     cudaError_t err;
     if (g.kind == TC_BF16)
-        err = fixed ? launch<TC_BF16, true>(ma, mb, p, s) : launch<TC_BF16, false>(ma, mb, p, s);
+        err = fixed ? (p.combined ? launch<TC_BF16, true, true>(ma, mb, p, s) : launch<TC_BF16, true, false>(ma, mb, p, s))
+                    : launch<TC_BF16, false, true>(ma, mb, p, s);
     else
-        err = fixed ? launch<TC_TF32, true>(ma, mb, p, s) : launch<TC_TF32, false>(ma, mb, p, s);
+        err = fixed ? (p.combined ? launch<TC_TF32, true, true>(ma, mb, p, s) : launch<TC_TF32, true, false>(ma, mb, p, s))
+                    : launch<TC_TF32, false, true>(ma, mb, p, s);
     if (err != cudaSuccess) return err;
     count_launch();
     return cudaGetLastError();
