@@ -6,9 +6,9 @@
 //
 // Operands are K-major slice stacks D[slice][row][pitch].  One CTA per SM owns a
 // 128 x 128 output tile at a time and issues tcgen05.mma.cta_group::1 (M = N = 128, 64 clocks
-// of the tensor pipe each) into its tensor memory.  The kernel is persistent: every CTA walks a
-// strided list of (tile, K-split) items.  (Pairs of SMs on one 256-row tile, cta_group::2, were
-// measured slower here: every slot of the operand rings then waits for handshakes between the
+// of the tensor pipe each) into its tensor memory.  The kernel is persistent: every CTA takes
+// (tile, K-split) items from a global counter, in raster order.  (Pairs of SMs on one 256-row
+// tile, cta_group::2, were measured slower here: every slot of the operand rings then waits for handshakes between the
 // two SMs, which cut the copy throughput per SM to about a third, and this GEMM streams about one
 // operand tile per slice product.)
 //
@@ -55,6 +55,7 @@
 #include <cudaTypedefs.h>
 #include <cuda_runtime.h>
 
+#include <atomic>
 #include <cstdlib>
 #include <mutex>
 #include <type_traits>
@@ -72,6 +73,8 @@ constexpr int B_TILE = BN * ROW_BYTES;         // 16 KB per B slice tile
 constexpr int NS = 6;                          // ring slots per operand
 constexpr int TILE_SMEM = NS * (A_TILE + B_TILE);  // 192 KB
 constexpr int MAX_SLICES = 8;
+constexpr int QN = 8;                          // item queue slots
+constexpr int kCounterSlots = 64;              // item counters, one per launch in flight
 constexpr int EPI_WARPS = 8;                   // two per TMEM lane quarter
 constexpr int EPI_THREADS = 32 * EPI_WARPS;
 constexpr int THREADS = 32 * 8 + EPI_THREADS;  // 512: producers, waiters and MMA issuer, then the epilogue
@@ -91,6 +94,8 @@ constexpr int kCombinedMaxK = 4096;
 
 enum OutKind { OUT_F64 = 0, OUT_I64 = 1, OUT_I64_RED = 2 };
 
+__device__ int g_item_counter[kCounterSlots];  // see the item schedule below
+
 struct SmemCtl {
     unsigned long long afull[NS], bfull[NS];
     unsigned long long empty[NS];              // slot s of both rings released
@@ -99,6 +104,10 @@ struct SmemCtl {
     unsigned int ready_a;                      // A tiles landed, in sequence order
     unsigned int ready_braw;                   // B tiles landed, in sequence order
     unsigned int ready_b;                      // B tiles landed with every A tile they meet
+    volatile int item_q[QN];                   // this CTA's items in order (-1: no work left)
+    unsigned int items_pub;                    // items written to item_q
+    unsigned int items_done;                   // items the epilogue has finished
+    volatile int epi_item;                     // the epilogue's current item, shared at its first epi_sync
     unsigned int tmem_base;
     volatile int abort;
     long long coloff[BN];                      // -1 for columns beyond N
@@ -119,6 +128,7 @@ struct Params {
     long long tri_rdiv, tri_cdiv;  // triangular tile skip (0 = off)
     int tiles_m, tiles_n, group_m, nitems;
     int combined;                  // host's choice of the kernel variant: combined landed count or both raw
+    int* counter;                  // next item to hand out (zero at launch)
     OutDesc out;
     int* status;
     unsigned long long wait_ns;
@@ -210,6 +220,26 @@ __device__ __forceinline__ bool landed(unsigned int* ctr, uint32_t idx, uint32_t
         if (BACKOFF) __nanosleep(32);  // a waiter's spin yields issue slots to its sub-partition
         known = observe(ctr);
         if ((int)(known - idx) > 0) return true;
+        if ((it & 15) == 0) {
+            if (ctl->abort) return false;
+            if (gtime() - t0 > p.wait_ns) {
+                ctl->abort = 1;
+                atomicOr(p.status, kStatusWaitExpired);
+                return false;
+            }
+        }
+    }
+}
+
+// Bounded spin until the shared count *ctr exceeds `v` (sleeping between looks: the caller is
+// not on the critical path); false on expiry or abort.
+__device__ __forceinline__ bool await_count(unsigned int* ctr, uint32_t v, SmemCtl* ctl, const Params& p)
+{
+    if ((int)(observe(ctr) - v) > 0) return true;
+    const unsigned long long t0 = gtime();
+    for (unsigned it = 1;; ++it) {
+        __nanosleep(64);
+        if ((int)(observe(ctr) - v) > 0) return true;
         if ((it & 15) == 0) {
             if (ctl->abort) return false;
             if (gtime() - t0 > p.wait_ns) {
@@ -325,7 +355,7 @@ __device__ __forceinline__ double pow2(int e)
 __device__ __forceinline__ void epi_sync() { asm volatile("bar.sync 1, %0;" ::"n"(EPI_THREADS) : "memory"); }
 
 // Work item i: K split i / (tiles_m tiles_n), tile i % (tiles_m tiles_n), rastered in groups
-// of group_m tile rows so that the pairs resident at once share A and B tiles in L2.
+// of group_m tile rows so that the items resident at once share A and B tiles in L2.
 struct Item {
     int split, m0, n0;
     bool skip;
@@ -349,6 +379,35 @@ __device__ __forceinline__ Item item_of(const Params& p, int i)
         it.skip = nmax / p.tri_cdiv < (long long)it.m0 / p.tri_rdiv;
     }
     return it;
+}
+
+// Items are handed out in order from a global counter, one at a time to whichever CTA asks
+// next, so that the items resident at once stay a contiguous run of the raster and share
+// their operand tiles in L2.  (A fixed stride of items per CTA let the CTAs drift apart over
+// thousands of items: a 42000 x 160000 x 2000 GEMM then read about 1.9 TB from HBM.)  One
+// producer thread fetches; every role reads the items from a queue in shared memory.
+
+// The fetching thread's item k: -1 when no work is left (or on abort).  Slot k % QN is
+// reused only after the epilogue, the last role to read the queue, has finished item k - QN.
+__device__ __forceinline__ int fetch_item(SmemCtl* ctl, const Params& p, uint32_t k)
+{
+    int item = -1;
+    if (k < QN || await_count(&ctl->items_done, k - QN, ctl, p)) {
+        do {
+            item = atomicAdd(p.counter, 1);
+        } while (item < p.nitems && item_of(p, item).skip);
+        if (item >= p.nitems) item = -1;
+    }
+    ctl->item_q[k % QN] = item;
+    publish(&ctl->items_pub, k + 1);
+    return item;
+}
+
+// Item k of this CTA for the other roles (-1: no work left, or abort).
+__device__ __forceinline__ int item_at(SmemCtl* ctl, const Params& p, uint32_t k)
+{
+    if (!await_count(&ctl->items_pub, k, ctl, p)) return -1;
+    return ctl->item_q[k % QN];
 }
 
 // Pass sequence of one item shared by all roles: groups in order, each cut into
@@ -478,7 +537,6 @@ gemm_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
 
     constexpr int KSTEP = KIND == TC_BF16 ? 64 : 32;  // K elements per 128-byte row
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int cta = (int)blockIdx.x, nctas = (int)gridDim.x;
 
     if (threadIdx.x == 0) {
         for (int s = 0; s < NS; ++s) {
@@ -491,6 +549,8 @@ gemm_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
         ctl->ready_a = 0;
         ctl->ready_b = 0;
         ctl->ready_braw = 0;
+        ctl->items_pub = 0;
+        ctl->items_done = 0;
         ctl->abort = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
@@ -533,9 +593,14 @@ gemm_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
                 tma_load_3d(ring + s * tile, map, &full[s], kb, row, slice);
                 return true;
             };
-            for (int item = cta; item < p.nitems && ok; item += nctas) {
+            // producer 0 fetches the items, item k + 1 as soon as item k starts, so that the
+            // fetch (a global atomic) overlaps item k's copies
+            int next = -1;
+            for (uint32_t k = 0; ok; ++k) {
+                const int item = prod == 0 ? (k == 0 ? fetch_item(ctl, p, 0) : next) : item_at(ctl, p, k);
+                if (item < 0) break;
+                if (prod == 0) next = fetch_item(ctl, p, k + 1);
                 const Item w = item_of(p, item);
-                if (w.skip) continue;
                 const int rowA = (int)(p.rowA0 + w.m0), rowB = (int)(p.rowB0 + w.n0);
                 PassIter it;
                 it.begin(p, w.split);
@@ -572,21 +637,23 @@ gemm_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
             // a barrier test blocks the issuing thread for about 70 ns, as long as two of its
             // MMAs take, and per-tile tests left the tensor pipe idle most of the time.  This one
             // counts the A tiles landed, in sequence order.
-            uint32_t total = 0;  // this CTA's A tiles (as many as its B tiles)
-            for (int item = cta; item < p.nitems; item += nctas) {
-                const Item w = item_of(p, item);
-                if (w.skip) continue;
+            uint32_t u = 0;  // A tiles waited for
+            bool ok = true;
+            for (uint32_t k = 0; ok; ++k) {
+                const int item = item_at(ctl, p, k);
+                if (item < 0) break;
+                uint32_t end = u;  // the item's A tiles (as many as its B tiles)
                 PassIter it;
-                it.begin(p, w.split);
+                it.begin(p, item_of(p, item).split);
                 do {
                     int lo, hi;
                     it.ranges(p, lo, hi);
-                    total += (uint32_t)((it.k1 - it.k0 + KSTEP - 1) / KSTEP) * (uint32_t)(hi - lo + 1);
+                    end += (uint32_t)((it.k1 - it.k0 + KSTEP - 1) / KSTEP) * (uint32_t)(hi - lo + 1);
                 } while (it.next(p));
-            }
-            for (uint32_t u = 0; u < total; ++u) {
-                if (!wait_fast(&ctl->afull[u % NS], (u / NS) & 1, ctl, p)) break;
-                publish(&ctl->ready_a, u + 1);
+                for (; u < end && ok; ++u) {
+                    ok = wait_fast(&ctl->afull[u % NS], (u / NS) & 1, ctl, p);
+                    if (ok) publish(&ctl->ready_a, u + 1);
+                }
             }
         } else if (warp == WARP_WAIT_B && lane == 0) {
             // The other counts the B tiles that have landed (raw) and, when the launch asks for
@@ -597,11 +664,11 @@ gemm_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
             // copies do (long K streamed from HBM: -15%, measured), so the host chooses.
             uint32_t nb = 0, a_done = 0, known_a = 0;  // B tiles published, A tiles of past K-steps
             bool ok = true;
-            for (int item = cta; item < p.nitems && ok; item += nctas) {
-                const Item w = item_of(p, item);
-                if (w.skip) continue;
+            for (uint32_t k = 0; ok; ++k) {
+                const int item = item_at(ctl, p, k);
+                if (item < 0) break;
                 PassIter it;
-                it.begin(p, w.split);
+                it.begin(p, item_of(p, item).split);
                 do {
                     int lo, hi;
                     it.ranges(p, lo, hi);
@@ -639,11 +706,11 @@ gemm_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
             st.known_b = 0;
             uint32_t npass = 0;
             bool ok = true, any = false;
-            for (int item = cta; item < p.nitems && ok; item += nctas) {
-                const Item w = item_of(p, item);
-                if (w.skip) continue;
+            for (uint32_t k = 0; ok; ++k) {
+                const int item = item_at(ctl, p, k);
+                if (item < 0) break;
                 PassIter it;
-                it.begin(p, w.split);
+                it.begin(p, item_of(p, item).split);
                 do {
                     int lo, hi;
                     it.ranges(p, lo, hi);  // lo = 0 and hi = the pass's top level
@@ -694,12 +761,20 @@ gemm_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
         acc_t sum[COLS_PER_THREAD];
         uint32_t npass = 0;
         bool ok = true;
-        // Every epilogue warp walks all items and meets every epi_sync even after an abort
-        // (it then skips the waits and TMEM reads), so no warp can be left at a named
+        // One thread reads each item from the queue and shares it at the item's first epi_sync,
+        // so every epilogue warp walks the same items and meets every epi_sync even after an
+        // abort (it then skips the waits and TMEM reads): no warp can be left at a named
         // barrier that a warp which gave up will never reach.
-        for (int item = cta; item < p.nitems; item += nctas) {
+        for (uint32_t k = 0;; ++k) {
+            if (e == 0 && lane == 0) {
+                // this thread has finished items 0 .. k-1 (the queue slots are read once per item)
+                if (k > 0) publish(&ctl->items_done, k);
+                ctl->epi_item = item_at(ctl, p, k);
+            }
+            epi_sync();
+            const int item = ctl->epi_item;
+            if (item < 0) break;
             const Item w = item_of(p, item);
-            if (w.skip) continue;
             // this item's output row and column tables (the previous item's writes are done)
             const int m = w.m0 + row;
             const long long ro = (m < p.M) ? map2(p.out.rmap, m) : -1;
@@ -939,8 +1014,18 @@ cudaError_t gemm_tc(const GemmTc& g, cudaStream_t s)
     p.group_m = p.tiles_m < 8 ? p.tiles_m : 8;
     p.combined = p.kper <= kCombinedMaxK ? 1 : 0;
     const long long nitems = (long long)p.tiles_m * p.tiles_n * p.ksplit;
-    if (nitems > 0x7fffffffll) return cudaErrorInvalidConfiguration;
+    // (the item counter runs past nitems by at most two per CTA)
+    if (nitems > 0x7fffffffll - (1 << 20)) return cudaErrorInvalidConfiguration;
     p.nitems = (int)nitems;
+    // item counter: a slot of a small ring (launches in flight on other streams take other
+    // slots), zeroed in stream order before the launch
+    static std::atomic<unsigned> next_slot{0};
+    int* counters = nullptr;
+    cudaError_t cerr = cudaGetSymbolAddress((void**)&counters, g_item_counter);
+    if (cerr != cudaSuccess) return cerr;
+    p.counter = counters + (next_slot.fetch_add(1) % kCounterSlots);
+    cerr = cudaMemsetAsync(p.counter, 0, sizeof(int), s);
+    if (cerr != cudaSuccess) return cerr;
     CUtensorMap ma, mb;
     if (!make_map(&ma, g.A, g.kind, g.K, g.pitchA, g.rowsA, g.slices, BM)) return cudaErrorInvalidValue;
     if (!make_map(&mb, g.B, g.kind, g.K, g.pitchB, g.rowsB, g.slices, BN)) return cudaErrorInvalidValue;
