@@ -89,8 +89,6 @@ constexpr int REG_LAUNCH = 128, REG_LOW = 64, REG_HIGH = 192;
 constexpr int WARP_WAIT_A = 1, WARP_WAIT_B = 5, WARP_MMA = 2;
 static_assert(256 * REG_LOW + 256 * REG_HIGH <= THREADS * REG_LAUNCH, "register split exceeds the launch's share");
 constexpr unsigned long long kDrainLimitNs = 1000000000ull;  // bound on the abort-path drains
-// Items of at most this much K use the combined landed count (see the waiters)
-constexpr int kCombinedMaxK = 4096;
 
 enum OutKind { OUT_F64 = 0, OUT_I64 = 1, OUT_I64_RED = 2 };
 
@@ -127,7 +125,6 @@ struct Params {
     int ksplit, kper;              // K split: item split s owns [s*kper, min(K, (s+1)*kper))
     long long tri_rdiv, tri_cdiv;  // triangular tile skip (0 = off)
     int tiles_m, tiles_n, group_m, nitems;
-    int combined;                  // host's choice of the kernel variant: combined landed count or both raw
     int* counter;                  // next item to hand out (zero at launch)
     OutDesc out;
     int* status;
@@ -467,7 +464,7 @@ __device__ __forceinline__ uint32_t slot_add(uint32_t a, int k)  // (a + k) % NS
 // with one commit.  HI >= 0 fixes the shape at compile time (the loops unroll and the slot
 // arithmetic folds -- with the shape at run time the issuing thread, not the tensor pipe, set
 // the pace); HI < 0 takes any shape at run time.
-template <int KIND, int HI, int NL, bool COMB>
+template <int KIND, int HI, int NL>
 __device__ __forceinline__ bool issue_kstep(IssueState& st, int hi_rt, int nl_rt, SmemCtl* ctl, const Params& p)
 {
     const int hi = HI >= 0 ? HI : hi_rt;
@@ -477,22 +474,15 @@ __device__ __forceinline__ bool issue_kstep(IssueState& st, int hi_rt, int nl_rt
     for (int j = 0; j <= hi; ++j) {
         const uint32_t idx = st.used + (uint32_t)j;
         const int imin = L1 - j > 0 ? L1 - j : 0;  // lowest A slice that B_j meets
-        if (COMB) {
+        if ((int)(st.known_b - idx) <= 0) {
+            st.known_b = observe(&ctl->ready_b);
             if ((int)(st.known_b - idx) <= 0) {
-                st.known_b = observe(&ctl->ready_b);
-                if ((int)(st.known_b - idx) <= 0) {
-                    // late tiles: watch the two raw counts, not the combined one, which would add
-                    // the second waiter's reaction to every late A tile
-                    if (!landed(&ctl->ready_a, st.used + (uint32_t)(hi - imin), st.known_a, ctl, p) ||
-                        !landed(&ctl->ready_braw, idx, st.known_braw, ctl, p))
-                        return false;
-                }
-                fence_after();
+                // late tiles: watch the two raw counts, not the combined one, which would add
+                // the second waiter's reaction to every late A tile
+                if (!landed(&ctl->ready_a, st.used + (uint32_t)(hi - imin), st.known_a, ctl, p) ||
+                    !landed(&ctl->ready_braw, idx, st.known_braw, ctl, p))
+                    return false;
             }
-        } else {
-            if (!landed(&ctl->ready_a, st.used + (uint32_t)(hi - imin), st.known_a, ctl, p) ||
-                !landed(&ctl->ready_braw, idx, st.known_braw, ctl, p))
-                return false;
             fence_after();
         }
         const uint32_t bs = slot_add(st.slot0, j);
@@ -517,15 +507,15 @@ __device__ __forceinline__ bool issue_kstep(IssueState& st, int hi_rt, int nl_rt
     return true;
 }
 
-template <int KIND, int HI, int NL, bool COMB>
+template <int KIND, int HI, int NL>
 __device__ __forceinline__ bool issue_pass(IssueState& st, int nk, int hi, int nl, SmemCtl* ctl, const Params& p)
 {
     for (int k = 0; k < nk; ++k)
-        if (!issue_kstep<KIND, HI, NL, COMB>(st, hi, nl, ctl, p)) return false;
+        if (!issue_kstep<KIND, HI, NL>(st, hi, nl, ctl, p)) return false;
     return true;
 }
 
-template <int KIND, bool FIXED, bool COMB>
+template <int KIND, bool FIXED>
 __global__ void __launch_bounds__(THREADS, 1)
 gemm_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, const Params p)
 {
@@ -656,12 +646,11 @@ gemm_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
                 }
             }
         } else if (warp == WARP_WAIT_B && lane == 0) {
-            // The other counts the B tiles that have landed (raw) and, when the launch asks for
-            // it, those that have landed together with every A tile they meet (the A count is
-            // the first thread's).  With the combined count the issuer makes one compare per B
-            // tile and reads the raw counts only when tiles are late: that pays where the issue
-            // loop sets the pace (short K per item, operands from L2: +10%), and costs where the
-            // copies do (long K streamed from HBM: -15%, measured), so the host chooses.
+            // The other counts the B tiles that have landed (raw) and those that have landed
+            // together with every A tile they meet (the A count is the first thread's).  The
+            // issuer compares the combined count once per B tile and reads the raw counts only
+            // when tiles are late (one compare instead of two measured +9% where the issue loop
+            // sets the pace).
             uint32_t nb = 0, a_done = 0, known_a = 0;  // B tiles published, A tiles of past K-steps
             bool ok = true;
             for (uint32_t k = 0; ok; ++k) {
@@ -678,9 +667,8 @@ gemm_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
                             const int imin = L1 - j > lo ? L1 - j : lo;  // lowest A slice B_j meets
                             ok = wait_fast(&ctl->bfull[nb % NS], (nb / NS) & 1, ctl, p);
                             if (ok) publish(&ctl->ready_braw, nb + 1);
-                            if (COMB)
-                                ok = ok && landed<true>(&ctl->ready_a, a_done + (uint32_t)(hi - imin), known_a, ctl, p);
-                            if (ok && COMB) publish(&ctl->ready_b, nb + 1);
+                            ok = ok && landed<true>(&ctl->ready_a, a_done + (uint32_t)(hi - imin), known_a, ctl, p);
+                            if (ok) publish(&ctl->ready_b, nb + 1);
                             ++nb;
                         }
                         a_done += (uint32_t)(hi - lo + 1);
@@ -723,12 +711,12 @@ gemm_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
                     st.fresh = (1u << nl) - 1;
                     const int nk = (it.k1 - it.k0 + KSTEP - 1) / KSTEP;
                     switch (hi * 4 + nl) {  // the shapes the host builds for up to 8 slices
-                        case 0 * 4 + 1: ok = issue_pass<KIND, 0, 1, COMB>(st, nk, hi, nl, ctl, p); break;
-                        case 1 * 4 + 2: ok = issue_pass<KIND, 1, 2, COMB>(st, nk, hi, nl, ctl, p); break;
-                        case 3 * 4 + 2: ok = issue_pass<KIND, 3, 2, COMB>(st, nk, hi, nl, ctl, p); break;
-                        case 5 * 4 + 2: ok = issue_pass<KIND, 5, 2, COMB>(st, nk, hi, nl, ctl, p); break;
-                        case 7 * 4 + 2: ok = issue_pass<KIND, 7, 2, COMB>(st, nk, hi, nl, ctl, p); break;
-                        default: ok = issue_pass<KIND, -1, 0, COMB>(st, nk, hi, nl, ctl, p); break;
+                        case 0 * 4 + 1: ok = issue_pass<KIND, 0, 1>(st, nk, hi, nl, ctl, p); break;
+                        case 1 * 4 + 2: ok = issue_pass<KIND, 1, 2>(st, nk, hi, nl, ctl, p); break;
+                        case 3 * 4 + 2: ok = issue_pass<KIND, 3, 2>(st, nk, hi, nl, ctl, p); break;
+                        case 5 * 4 + 2: ok = issue_pass<KIND, 5, 2>(st, nk, hi, nl, ctl, p); break;
+                        case 7 * 4 + 2: ok = issue_pass<KIND, 7, 2>(st, nk, hi, nl, ctl, p); break;
+                        default: ok = issue_pass<KIND, -1, 0>(st, nk, hi, nl, ctl, p); break;
                     }
                     if (!ok) break;
                     any = true;
@@ -898,19 +886,19 @@ bool make_map(CUtensorMap* m, const void* base, int kind, long long K, long long
     return r == CUDA_SUCCESS;
 }
 
-template <int KIND, bool FIXED, bool COMB>
+template <int KIND, bool FIXED>
 cudaError_t launch(const CUtensorMap& ma, const CUtensorMap& mb, const Params& p, cudaStream_t s)
 {
     static std::once_flag once;
     static cudaError_t attr_err = cudaSuccess;
     static int max_ctas = 0;
     std::call_once(once, [] {
-        attr_err = cudaFuncSetAttribute(gemm_tc_kernel<KIND, FIXED, COMB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+        attr_err = cudaFuncSetAttribute(gemm_tc_kernel<KIND, FIXED>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                         (int)SMEM_BYTES);
         // persistent: as many CTAs as are resident on the device at once (one per SM)
         int per_sm = 0;
         if (attr_err != cudaSuccess ||
-            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, gemm_tc_kernel<KIND, FIXED, COMB>, THREADS, SMEM_BYTES) !=
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, gemm_tc_kernel<KIND, FIXED>, THREADS, SMEM_BYTES) !=
                 cudaSuccess ||
             per_sm <= 0) {
             cudaGetLastError();
@@ -920,7 +908,7 @@ cudaError_t launch(const CUtensorMap& ma, const CUtensorMap& mb, const Params& p
     });
     if (attr_err != cudaSuccess) return attr_err;
     const int ctas = p.nitems < max_ctas ? p.nitems : max_ctas;
-    gemm_tc_kernel<KIND, FIXED, COMB><<<ctas, THREADS, SMEM_BYTES, s>>>(ma, mb, p);
+    gemm_tc_kernel<KIND, FIXED><<<ctas, THREADS, SMEM_BYTES, s>>>(ma, mb, p);
     return cudaGetLastError();
 }
 
@@ -1012,7 +1000,6 @@ cudaError_t gemm_tc(const GemmTc& g, cudaStream_t s)
     p.tiles_m = (g.M + BM - 1) / BM;
     p.tiles_n = (g.N + BN - 1) / BN;
     p.group_m = p.tiles_m < 8 ? p.tiles_m : 8;
-    p.combined = p.kper <= kCombinedMaxK ? 1 : 0;
     const long long nitems = (long long)p.tiles_m * p.tiles_n * p.ksplit;
     // (the item counter runs past nitems by at most two per CTA)
     if (nitems > 0x7fffffffll - (1 << 20)) return cudaErrorInvalidConfiguration;
@@ -1031,11 +1018,9 @@ cudaError_t gemm_tc(const GemmTc& g, cudaStream_t s)
     if (!make_map(&mb, g.B, g.kind, g.K, g.pitchB, g.rowsB, g.slices, BN)) return cudaErrorInvalidValue;
     cudaError_t err;
     if (g.kind == TC_BF16)
-        err = fixed ? (p.combined ? launch<TC_BF16, true, true>(ma, mb, p, s) : launch<TC_BF16, true, false>(ma, mb, p, s))
-                    : launch<TC_BF16, false, true>(ma, mb, p, s);
+        err = fixed ? launch<TC_BF16, true>(ma, mb, p, s) : launch<TC_BF16, false>(ma, mb, p, s);
     else
-        err = fixed ? (p.combined ? launch<TC_TF32, true, true>(ma, mb, p, s) : launch<TC_TF32, true, false>(ma, mb, p, s))
-                    : launch<TC_TF32, false, true>(ma, mb, p, s);
+        err = fixed ? launch<TC_TF32, true>(ma, mb, p, s) : launch<TC_TF32, false>(ma, mb, p, s);
     if (err != cudaSuccess) return err;
     count_launch();
     return cudaGetLastError();
