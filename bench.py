@@ -182,9 +182,9 @@ def cpu_model() -> str:
 
 
 def traffic_record():
-    """DRAM bytes over algorithmic bytes of the tensor-core GEMM, from the committed summary of one
-    small-case ncu capture (profiles/gemm_tc_traffic.json), if the kernel source is unchanged since
-    it was captured (else None)."""
+    """DRAM bytes over algorithmic bytes of the tensor-core GEMM, from the committed summary of an
+    ncu capture (profiles/gemm_tc_traffic.json), if the kernel source is unchanged since it was
+    captured (else None)."""
     import hashlib
     p = os.path.join(ROOT, "profiles", "gemm_tc_traffic.json")
     if not os.path.exists(p):
@@ -292,8 +292,8 @@ def run_ours(a):
                 "unit": "TFLOP/s", "frac": (achieved / peak) if achieved else None,
                 "traffic": tr["ratio"] * alg_bytes if tr else None,
                 "algorithmic_bytes_per_launch": alg_bytes,
-                "traffic_source": (f"ncu dram__bytes_read+write of one small-case launch ({tr['launch']}): "
-                                   f"{tr['ratio']:.2f} x its algorithmic bytes, applied to this workload's "
+                "traffic_source": (f"ncu dram__bytes_read+write ({tr['launch']}, {tr['workload']}): "
+                                   f"{tr['ratio']:.2f} x their algorithmic bytes, applied to this run's "
                                    "algorithmic bytes per launch") if tr else None,
                 "peak_source": f"{pk_src} bf16_tflops_sustained (kernel timed inside a long step), of measured"
                                if pk_src == "measured" else "fallback 1.7 PFLOP/s sustained, of fallback",

@@ -552,7 +552,11 @@ int run_tc(const char* name, const Ctx& c, int M, int N, int K, const Operand& A
             // drift apart and re-read the rows from HBM.  Items are ordered split-major, so
             // short splits keep the resident items within one K window: a 36540 x 820 x 80200
             // GEMM measured 1080 TFLOP/s issued unsplit, 1130 with splits of 8192, 1200 with 2048.
-            if (tiles > nsm)
+            // Not for intermediates (the integral blocks): there the split's zeroing pass and
+            // red.global adds on the large int64 output cost more than the reuse gains (o=60,
+            // v=600, n=3000: KG1 6.58 s split, 5.87 s whole; its R+- GEMMs 3.48 s split, 4.81 s
+            // whole).
+            if (tiles > nsm && !intermediate)
                 while ((K + best - 1) / best > kReuseK) ++best;
             if (best > 1) {
                 // the kernel rounds a split up to whole K-steps: count the splits that leaves
