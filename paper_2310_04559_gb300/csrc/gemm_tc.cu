@@ -8,9 +8,9 @@
 // 128 x 128 output tile at a time and issues tcgen05.mma.cta_group::1 (M = N = 128, 64 clocks
 // of the tensor pipe each) into its tensor memory.  The kernel is persistent: every CTA takes
 // (tile, K-split) items from a global counter, in raster order.  (Pairs of SMs on one 256-row
-// tile, cta_group::2, were measured slower here: every slot of the operand rings then waits for handshakes between the
-// two SMs, which cut the copy throughput per SM to about a third, and this GEMM streams about one
-// operand tile per slice product.)
+// tile, cta_group::2, were measured slower here: every slot of the operand rings then waits for
+// handshakes between the two SMs, which cut the copy throughput per SM to about a third, and this
+// GEMM streams about one operand tile per slice product.)
 //
 // Passes.  The slice-product levels L (products A_i B_j with i + j = L) are
 // processed in groups of at most two; a "pass" is one group over one K-chunk, and
